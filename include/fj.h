@@ -1,0 +1,191 @@
+/*
+ * fj.h - C ABI of the GB300 Friedkin-Johnsen solver library (libfj.so).
+ *
+ * The library evaluates the opinion-dynamics quantities of Xu, Bao and Zhang,
+ * "Fast Evaluation for Relevant Quantities of Opinion Dynamics" (WWW 2021):
+ *
+ *   graph    G = (V, E, w), undirected, weights w_e > 0            (Sec. 2.1)
+ *   L        = D - A = B^T W B, the weighted Laplacian              (Sec. 2.1)
+ *   z        = (I + L)^-1 s, the FJ equilibrium opinions     (Eq. FJmodel02)
+ *   C_I      = sum_i (z_i - s_i)^2          internal conflict  (Sec. 3.2)
+ *   D        = sum_{(i,j) in E} w_ij (z_i - z_j)^2 disagreement (Sec. 3.2)
+ *   P        = sum_i (z_i - mean(z))^2      polarization       (Sec. 3.2)
+ *   C        = sum_i z_i^2                  controversy        (Sec. 3.2)
+ *   I_dc     = D + C                        disagreement-controversy index
+ *
+ * Algorithm 1 (APPROXIM) reduces the quantities to two Laplacian solves and
+ * five squared l2 norms (Lemma PropA).  This library computes the same five
+ * numbers from ONE centred solve q = (I + L)^-1 s_bar, s_bar = s - mean(s) 1:
+ * because Omega 1 = 1 (Sec. 2.2), z = q + mean(s) 1 exactly, and
+ *   P = ||q||^2, C = ||q + mean(s) 1||^2, C_I = ||s_bar - q||^2,
+ *   D = ||W^1/2 B q||^2, I_dc = D + C.
+ * The solve is Jacobi-preconditioned conjugate gradients on the GPU, with
+ * float32 inner iterations refined by float64 residuals (or all float64).
+ * The paper's accuracy parameter delta (Algorithm 1, first step) is replaced
+ * by a relative-residual target ||s_bar - (I + L) q||_2 <= tol ||s_bar||_2.
+ *
+ * Conventions for every call:
+ *   - Return value: FJ_OK (0) on success, FJ_PENDING (1) from fj_poll while a
+ *     request runs, a negative FJ_ERR_* code otherwise.  After an error,
+ *     fj_last_error() gives a message for the calling thread.
+ *   - Pointers named "host or device" are read according to the FJ_*_PTRS
+ *     flag passed with them.  Device pointers must belong to the context's
+ *     device.  Inputs are copied or consumed before the call returns (except
+ *     where a call says otherwise); the caller keeps ownership of its buffers.
+ *   - All GPU work of a context runs on the context's stream (fj_set_stream).
+ *     fj_solve / fj_quantities return only after their results are written.
+ *   - A context must not be used from two threads at once; distinct contexts
+ *     are independent.
+ */
+#ifndef FJ_H
+#define FJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t fj_status;
+
+enum {
+  FJ_OK = 0,
+  FJ_PENDING = 1,              /* fj_poll: request not finished yet          */
+  FJ_ERR_ARG = -1,             /* null pointer, n <= 0, bad size/flag        */
+  FJ_ERR_GRAPH = -2,           /* node id out of range, weight <= 0/NaN/Inf  */
+  FJ_ERR_OOM = -3,             /* device allocation failed                   */
+  FJ_ERR_ADMIT = -4,           /* request larger than the serving budget     */
+  FJ_ERR_NOT_CONVERGED = -5,   /* iteration caps reached before tol          */
+  FJ_ERR_NUMERIC = -6,         /* NaN or Inf met in the iteration            */
+  FJ_ERR_TIMEOUT = -7,         /* a bounded device-side wait gave up         */
+  FJ_ERR_CUDA = -8,            /* a CUDA runtime call failed                 */
+  FJ_ERR_TICKET = -9           /* unknown or already collected ticket        */
+};
+
+/* Where a call's pointers live. */
+#define FJ_HOST_PTRS 0u
+#define FJ_DEVICE_PTRS 1u
+
+/* Arithmetic of the solve (fj_opts.precision). */
+enum {
+  FJ_PREC_MIXED = 0, /* float32 PCG inner iterations, float64 residual
+                        refinement: results to `tol` like FP64 (default)     */
+  FJ_PREC_FP64 = 1,  /* float64 throughout: the plain reference solve        */
+  FJ_PREC_FP32 = 2   /* float32 PCG only; float64 used only for the final
+                        residual and the quantity sums                        */
+};
+
+typedef struct fj_ctx fj_ctx;     /* device, stream, workspace               */
+typedef struct fj_graph fj_graph; /* device-resident CSR of I + L            */
+
+typedef struct fj_opts {
+  double tol;         /* target ||s_bar - (I+L) q|| / ||s_bar|| (1e-10)      */
+  double inner_tol;   /* residual reduction per float32 inner solve (1e-5)   */
+  int32_t precision;  /* FJ_PREC_* (FJ_PREC_MIXED)                           */
+  int32_t max_iter;   /* cap on inner iterations over the whole solve (20000)*/
+  int32_t max_refine; /* cap on float64 refinement steps (12)                */
+  uint32_t flags;     /* FJ_HOST_PTRS or FJ_DEVICE_PTRS for s, z             */
+} fj_opts;
+
+typedef struct fj_info {
+  int32_t iterations;  /* inner PCG iterations (all refinement steps)        */
+  int32_t refinements; /* float64 residual evaluations                       */
+  double rel_residual; /* final ||s_bar-(I+L)q||/||s_bar||, max over columns */
+  double device_ms;    /* device time of the solve kernels                   */
+  int32_t status;      /* same as the return value of the call               */
+  int32_t columns;     /* k                                                  */
+} fj_info;
+
+/* The five quantities of one opinion vector (Sec. 3.2 definitions). */
+typedef struct fj_quant {
+  double C_I;  /* internal conflict        */
+  double D;    /* disagreement             */
+  double P;    /* polarization             */
+  double C;    /* controversy              */
+  double I_dc; /* disagreement-controversy */
+} fj_quant;
+
+/* Fills *opts with the defaults listed in fj_opts. */
+void fj_default_opts(fj_opts* opts);
+
+/* Thread-local text of the last error raised on this thread ("" if none). */
+const char* fj_last_error(void);
+
+/* Library version string. */
+const char* fj_version(void);
+
+/* Creates a context on CUDA device `device` with its own non-blocking stream.
+ * The context owns a workspace that grows to the largest solve it has run.
+ * Errors: FJ_ERR_ARG (bad device / null out), FJ_ERR_CUDA. */
+fj_status fj_create(int device, fj_ctx** out);
+
+/* Waits for the context's stream, frees its workspace and the context.
+ * Graphs created on it must be freed first (fj_graph_free); requests still
+ * queued by fj_submit are cancelled. */
+fj_status fj_destroy(fj_ctx* ctx);
+
+/* Runs the context's later GPU work on `stream` (a cudaStream_t of the
+ * context's device; NULL restores the context's own stream). */
+fj_status fj_set_stream(fj_ctx* ctx, void* stream);
+
+/* Caps the number of thread blocks of the persistent solve kernel (0, the
+ * default, uses every block that can be co-resident on the device).  Lets
+ * several contexts run solves side by side on one GPU.
+ * Errors: FJ_ERR_ARG (NULL ctx or negative cap). */
+fj_status fj_set_max_blocks(fj_ctx* ctx, int32_t max_blocks);
+
+/* Builds the device CSR of I + L for an undirected weighted graph given as an
+ * edge list (Sec. 2.1: A, d_i = sum_j w_ij, L = D - A).
+ *   n        number of nodes (1 <= n <= 2^31 - 2)
+ *   m        number of listed undirected edges (>= 0); each edge once
+ *   src,dst  int32[m] endpoints in [0, n) (host or device, see flags)
+ *   w        float32[m] weights > 0 and finite, or NULL for unit weights
+ *   flags    FJ_HOST_PTRS or FJ_DEVICE_PTRS
+ * Self-loops are dropped (b_e = 0 adds nothing to L).  A repeated pair is a
+ * parallel edge: its weights add, as in L = sum_e w_e b_e b_e^T.  The graph
+ * need not be connected.  2 * m (minus self-loops) must stay below 2^31.
+ * The graph lives in device memory until fj_graph_free.
+ * Errors: FJ_ERR_ARG, FJ_ERR_GRAPH (bad id or weight; nothing allocated
+ * remains), FJ_ERR_OOM, FJ_ERR_CUDA. */
+fj_status fj_graph_upload(fj_ctx* ctx, int64_t n, int64_t m,
+                          const int32_t* src, const int32_t* dst,
+                          const float* w, uint32_t flags, fj_graph** out);
+
+/* Frees a graph made by fj_graph_upload on this context. */
+fj_status fj_graph_free(fj_ctx* ctx, fj_graph* g);
+
+/* Size of a graph: nodes, stored off-diagonal CSR entries (2 x non-loop
+ * edges), and whether it carries a weight array (0 = unit weights). */
+fj_status fj_graph_stats(const fj_graph* g, int64_t* n, int64_t* nnz,
+                         int32_t* weighted);
+
+/* Solves (I + L) z = s for k opinion vectors (Eq. FJmodel02) and optionally
+ * returns z and the five quantities of each column.
+ *   s     float64[n*k], column-major (column c at s + c*n), host or device
+ *   z     float64[n*k] output, same layout and location as s, or NULL
+ *   quant fj_quant[k] output in HOST memory, or NULL
+ *   opts  options (NULL: defaults); opts->flags says where s and z live
+ *   info  optional host output
+ * Any finite s is accepted (the paper assumes s in [0,1]; the algebra does
+ * not need it).  Errors: FJ_ERR_ARG, FJ_ERR_OOM, FJ_ERR_NOT_CONVERGED (z and
+ * quant still hold the last iterate), FJ_ERR_NUMERIC, FJ_ERR_TIMEOUT,
+ * FJ_ERR_CUDA. */
+fj_status fj_solve_ex(fj_ctx* ctx, const fj_graph* g, int32_t k,
+                      const double* s, double* z, fj_quant* quant,
+                      const fj_opts* opts, fj_info* info);
+
+/* fj_solve_ex with quant = NULL: the equilibrium z = (I + L)^-1 s. */
+fj_status fj_solve(fj_ctx* ctx, const fj_graph* g, int32_t k, const double* s,
+                   double* z, const fj_opts* opts, fj_info* info);
+
+/* fj_solve_ex with z = NULL: Algorithm 1's five outputs for each column of s
+ * (out: fj_quant[k] in host memory). */
+fj_status fj_quantities(fj_ctx* ctx, const fj_graph* g, int32_t k,
+                        const double* s, fj_quant* out, const fj_opts* opts,
+                        fj_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FJ_H */

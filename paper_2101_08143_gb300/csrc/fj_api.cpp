@@ -1,0 +1,369 @@
+// fj_api.cpp - the extern "C" entry points declared in include/fj.h.
+//
+// A context owns a device, a stream and one grow-only workspace that every
+// solve carves its vectors from, so the solve path allocates nothing once the
+// workspace has reached the size of the largest problem seen.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fj_internal.cuh"
+
+// defined in fj_graph.cu / fj_solve.cu
+fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m,
+                                const int32_t* src, const int32_t* dst, const float* w,
+                                fj_graph** out);
+fj_status fj_free_graph_device(fj_graph* g, cudaStream_t st);
+size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms);
+fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k,
+                          const double* s, double* z, double* quant, double* resid, int* status,
+                          char* ws, size_t ws_bytes, const fj_opts& o, int* launches_out,
+                          int max_blocks);
+
+namespace fj {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+fj_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("CUDA error in %s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FJ_ERR_OOM : FJ_ERR_CUDA;
+}
+
+}  // namespace fj
+
+using namespace fj;
+
+struct fj_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t own = nullptr;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;  // solver workspace
+  size_t ws_bytes = 0;
+  char* small = nullptr;  // quantities, residuals, status words
+  size_t small_bytes = 0;
+  double* s_dev = nullptr;  // staging of host s / z
+  size_t s_bytes = 0;
+  double* z_dev = nullptr;
+  size_t z_bytes = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int max_blocks = 0;  // 0: all co-resident blocks
+};
+
+namespace {
+
+fj_status grow(void** p, size_t* have, size_t need) {
+  if (*have >= need) return FJ_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  size_t sz = std::max(need, (size_t)4096);
+  cudaError_t e = cudaMalloc(p, sz);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("out of device memory (%zu bytes)", sz);
+    return FJ_ERR_OOM;
+  }
+  *have = sz;
+  return FJ_OK;
+}
+
+int decomposition(int32_t k, int* Ks) {
+  int cnt = 0, col = 0;
+  while (col < k) {
+    int K = 32;
+    while (K > k - col) K >>= 1;
+    Ks[cnt++] = K;
+    col += K;
+  }
+  return cnt;
+}
+
+fj_status status_from_bits(int bits) {
+  if (bits & kErrTimeout) {
+    set_error("a device-side wait timed out (solve abandoned)");
+    return FJ_ERR_TIMEOUT;
+  }
+  if (bits & kErrNumeric) {
+    set_error("NaN or Inf met in the iteration");
+    return FJ_ERR_NUMERIC;
+  }
+  if (bits & kErrNotConverged) {
+    set_error("iteration caps reached before the residual target");
+    return FJ_ERR_NOT_CONVERGED;
+  }
+  return FJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fj_default_opts(fj_opts* o) {
+  if (!o) return;
+  o->tol = 1e-10;
+  o->inner_tol = 1e-5;
+  o->precision = FJ_PREC_MIXED;
+  o->max_iter = 20000;
+  o->max_refine = 12;
+  o->flags = FJ_HOST_PTRS;
+}
+
+const char* fj_last_error(void) { return g_last_error.c_str(); }
+
+const char* fj_version(void) { return "fj-gb300 0.1 (sm_103a)"; }
+
+fj_status fj_create(int device, fj_ctx** out) {
+  if (!out) {
+    set_error("fj_create: out is NULL");
+    return FJ_ERR_ARG;
+  }
+  *out = nullptr;
+  int count = 0;
+  FJ_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) {
+    set_error("fj_create: device %d not present (%d devices)", device, count);
+    return FJ_ERR_ARG;
+  }
+  FJ_CUDA(cudaSetDevice(device));
+  fj_ctx* c = new fj_ctx();
+  c->device = device;
+  cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "fj_create");
+  }
+  c->stream = c->own;
+  *out = c;
+  return FJ_OK;
+}
+
+fj_status fj_destroy(fj_ctx* c) {
+  if (!c) return FJ_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (c->ws) cudaFree(c->ws);
+  if (c->small) cudaFree(c->small);
+  if (c->s_dev) cudaFree(c->s_dev);
+  if (c->z_dev) cudaFree(c->z_dev);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+  return FJ_OK;
+}
+
+fj_status fj_set_stream(fj_ctx* c, void* stream) {
+  if (!c) {
+    set_error("fj_set_stream: ctx is NULL");
+    return FJ_ERR_ARG;
+  }
+  c->stream = stream ? (cudaStream_t)stream : c->own;
+  return FJ_OK;
+}
+
+// Caps the persistent grid (0 = every co-resident block).  Lets several
+// contexts share the GPU at once; also used by tests.
+fj_status fj_set_max_blocks(fj_ctx* c, int32_t max_blocks) {
+  if (!c || max_blocks < 0) {
+    set_error("fj_set_max_blocks: bad argument");
+    return FJ_ERR_ARG;
+  }
+  c->max_blocks = max_blocks;
+  return FJ_OK;
+}
+
+fj_status fj_graph_upload(fj_ctx* c, int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                          const float* w, uint32_t flags, fj_graph** out) {
+  if (!c || !out) {
+    set_error("fj_graph_upload: ctx or out is NULL");
+    return FJ_ERR_ARG;
+  }
+  *out = nullptr;
+  if (n < 1 || n > (int64_t)INT32_MAX - 1 || m < 0 || 2 * m > (int64_t)INT32_MAX - 64) {
+    set_error("fj_graph_upload: need 1 <= n < 2^31-1 and 0 <= 2m < 2^31-64 (n=%lld, m=%lld)",
+              (long long)n, (long long)m);
+    return FJ_ERR_ARG;
+  }
+  if (m > 0 && (!src || !dst)) {
+    set_error("fj_graph_upload: src/dst is NULL");
+    return FJ_ERR_ARG;
+  }
+  if (flags & ~FJ_DEVICE_PTRS) {
+    set_error("fj_graph_upload: unknown flags 0x%x", flags);
+    return FJ_ERR_ARG;
+  }
+  FJ_CUDA(cudaSetDevice(c->device));
+  if (flags & FJ_DEVICE_PTRS)
+    return fj_build_graph_device(c->device, c->stream, n, m, src, dst, w, out);
+  // host edge list: copy it to the device first
+  int32_t *ds = nullptr, *dd = nullptr;
+  float* dw = nullptr;
+  const size_t eb = (size_t)std::max<int64_t>(m, 1) * 4;
+  if (cudaMallocAsync(&ds, eb, c->stream) != cudaSuccess ||
+      cudaMallocAsync(&dd, eb, c->stream) != cudaSuccess ||
+      (w && cudaMallocAsync(&dw, eb, c->stream) != cudaSuccess)) {
+    cudaGetLastError();
+    if (ds) cudaFreeAsync(ds, c->stream);
+    if (dd) cudaFreeAsync(dd, c->stream);
+    set_error("fj_graph_upload: out of device memory for the edge list");
+    return FJ_ERR_OOM;
+  }
+  fj_status rc = FJ_OK;
+  if (m > 0) {
+    cudaError_t e = cudaMemcpyAsync(ds, src, m * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dd, dst, m * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && w) e = cudaMemcpyAsync(dw, w, m * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "fj_graph_upload copy");
+  }
+  if (rc == FJ_OK) rc = fj_build_graph_device(c->device, c->stream, n, m, ds, dd, w ? dw : nullptr, out);
+  cudaFreeAsync(ds, c->stream);
+  cudaFreeAsync(dd, c->stream);
+  if (dw) cudaFreeAsync(dw, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return rc;
+}
+
+fj_status fj_graph_free(fj_ctx* c, fj_graph* g) {
+  if (!c) {
+    set_error("fj_graph_free: ctx is NULL");
+    return FJ_ERR_ARG;
+  }
+  if (!g) return FJ_OK;
+  FJ_CUDA(cudaSetDevice(c->device));
+  return fj_free_graph_device(g, c->stream);
+}
+
+fj_status fj_graph_stats(const fj_graph* g, int64_t* n, int64_t* nnz, int32_t* weighted) {
+  if (!g) {
+    set_error("fj_graph_stats: graph is NULL");
+    return FJ_ERR_ARG;
+  }
+  if (n) *n = g->n;
+  if (nnz) *nnz = g->nnz;
+  if (weighted) *weighted = g->weighted;
+  return FJ_OK;
+}
+
+fj_status fj_solve_ex(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, double* z,
+                      fj_quant* quant, const fj_opts* opts, fj_info* info) {
+  if (info) memset(info, 0, sizeof(*info));
+  if (!c || !g || !s || k < 1) {
+    set_error("fj_solve: ctx, graph and s must be non-NULL and k >= 1");
+    return FJ_ERR_ARG;
+  }
+  if (g->device != c->device) {
+    set_error("fj_solve: graph belongs to device %d, context to %d", g->device, c->device);
+    return FJ_ERR_ARG;
+  }
+  fj_opts o;
+  fj_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || o.max_iter < 1 ||
+      o.max_refine < 1 || o.precision < 0 || o.precision > 2 || (o.flags & ~FJ_DEVICE_PTRS)) {
+    set_error("fj_solve: invalid options");
+    return FJ_ERR_ARG;
+  }
+  FJ_CUDA(cudaSetDevice(c->device));
+  const int64_t n = g->n;
+  int Ks[64];
+  const int launches = decomposition(k, Ks);
+  const int inner_bytes = o.precision == FJ_PREC_FP64 ? 8 : 4;
+  size_t need = 0;
+  for (int i = 0; i < launches; ++i)
+    need = std::max(need, fj_solve_workspace_bytes(g, Ks[i], inner_bytes, c->num_sms));
+  fj_status rc = grow((void**)&c->ws, &c->ws_bytes, need);
+  if (rc != FJ_OK) return rc;
+  const size_t small_need = (size_t)k * 5 * 8 + (size_t)k * 8 + (size_t)launches * 3 * 4 + 1024;
+  rc = grow((void**)&c->small, &c->small_bytes, small_need);
+  if (rc != FJ_OK) return rc;
+  double* dq = (double*)c->small;
+  double* dres = dq + (size_t)k * 5;
+  int* dstat = (int*)(dres + k);
+
+  const bool host = !(o.flags & FJ_DEVICE_PTRS);
+  const double* sd = s;
+  double* zd = z;
+  const size_t vec_bytes = (size_t)n * k * 8;
+  if (host) {
+    rc = grow((void**)&c->s_dev, &c->s_bytes, vec_bytes);
+    if (rc != FJ_OK) return rc;
+    FJ_CUDA(cudaMemcpyAsync(c->s_dev, s, vec_bytes, cudaMemcpyHostToDevice, c->stream));
+    sd = c->s_dev;
+    if (z) {
+      rc = grow((void**)&c->z_dev, &c->z_bytes, vec_bytes);
+      if (rc != FJ_OK) return rc;
+      zd = c->z_dev;
+    }
+  }
+  FJ_CUDA(cudaMemsetAsync(dstat, 0, (size_t)launches * 3 * 4, c->stream));
+  FJ_CUDA(cudaEventRecord(c->ev0, c->stream));
+  int done_launches = 0;
+  rc = fj_solve_device(g, c->stream, c->num_sms, k, sd, zd, dq, dres, dstat, c->ws, c->ws_bytes, o,
+                       &done_launches, c->max_blocks);
+  if (rc != FJ_OK) return rc;
+  FJ_CUDA(cudaEventRecord(c->ev1, c->stream));
+  std::vector<double> hq((size_t)k * 5), hres(k);
+  std::vector<int> hstat((size_t)launches * 3);
+  FJ_CUDA(cudaMemcpyAsync(hq.data(), dq, hq.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  FJ_CUDA(cudaMemcpyAsync(hres.data(), dres, hres.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  FJ_CUDA(cudaMemcpyAsync(hstat.data(), dstat, hstat.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (host && z) FJ_CUDA(cudaMemcpyAsync(z, zd, vec_bytes, cudaMemcpyDeviceToHost, c->stream));
+  FJ_CUDA(cudaStreamSynchronize(c->stream));
+  int bits = 0, iters = 0, refines = 0;
+  for (int i = 0; i < launches; ++i) {
+    bits |= hstat[3 * i];
+    iters = std::max(iters, hstat[3 * i + 1]);
+    refines = std::max(refines, hstat[3 * i + 2]);
+  }
+  double worst = 0.0;
+  for (int j = 0; j < k; ++j) worst = std::max(worst, hres[j]);
+  if (quant) memcpy(quant, hq.data(), hq.size() * 8);
+  rc = status_from_bits(bits);
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->iterations = iters;
+    info->refinements = refines;
+    info->rel_residual = worst;
+    info->device_ms = ms;
+    info->status = rc;
+    info->columns = k;
+  }
+  return rc;
+}
+
+fj_status fj_solve(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, double* z,
+                   const fj_opts* opts, fj_info* info) {
+  return fj_solve_ex(c, g, k, s, z, nullptr, opts, info);
+}
+
+fj_status fj_quantities(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, fj_quant* out,
+                        const fj_opts* opts, fj_info* info) {
+  if (!out) {
+    set_error("fj_quantities: out is NULL");
+    return FJ_ERR_ARG;
+  }
+  return fj_solve_ex(c, g, k, s, nullptr, out, opts, info);
+}
+
+}  // extern "C"

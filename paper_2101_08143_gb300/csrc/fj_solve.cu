@@ -1,0 +1,592 @@
+// fj_solve.cu - persistent Jacobi-PCG solve of (I + L) q = s_bar and the five
+// FJ quantities (Eq. FJmodel02, Sec. 3.2, Algorithm 1).
+//
+// One cooperative launch runs the whole solve for K right-hand sides:
+//
+//   setup     mu = 1^T s / n, s_bar = s - mu 1               (Alg. 1, step 2)
+//   refine    repeat: r64 = s_bar - (I+L) q        (float64 residual walk)
+//               inner Jacobi-PCG on (I+L) e = r64 in the inner precision,
+//               q += e                                 (iterative refinement)
+//   output    z = q + mu 1 (Omega 1 = 1, Sec. 2.2), and from the last
+//             residual pass: P = ||q||^2, C = ||q + mu 1||^2,
+//             C_I = ||s_bar - q||^2, D = 1/2 sum_CSR w (q_i - q_j)^2
+//             (= ||W^1/2 B q||^2, Lemma PropA), I_dc = D + C.
+//
+// The inner solver is the Chronopoulos-Gear form of preconditioned CG: both
+// inner products of an iteration come out of one grid-wide reduction, so an
+// iteration costs two grid barriers (vector update | SpMV walk).  The SpMV
+// reduction (w, u) is taken as u^T u + 1/2 sum_CSR w (u_i - u_j)^2, which the
+// merge-path walk produces without waiting for split rows to be combined.
+//
+// All reductions are two-level and in a fixed order (per block, then over
+// blocks), and every block evaluates the same scalars, so control flow is
+// identical in all blocks and results are bit-reproducible.
+#include <algorithm>
+
+#include "fj_internal.cuh"
+#include "fj_walk.cuh"
+
+namespace fj {
+
+constexpr int kWarps = 16;
+constexpr int kThreads = kWarps * 32;
+constexpr int kMaxBlocksPerSM = 4;
+constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s per barrier wait
+
+enum Slot {
+  S_SUM = 0,  // column sums of s
+  S_BB,       // ||s_bar||^2
+  S_GAM,      // (r, u)
+  S_RR,       // (r, r) inner
+  S_UU,       // (u, u)
+  S_EQ,       // 1/2 sum_CSR w (u_i - u_j)^2 times 2 (raw walk sum)
+  S_RR64,     // ||r64||^2
+  S_P,        // ||q||^2
+  S_C,        // ||q + mu||^2
+  S_CI,       // ||s_bar - q||^2
+  S_D,        // raw walk sum of w (q_i - q_j)^2 over CSR entries
+  NSLOT
+};
+
+enum Mode { kModeMixed = 0, kModeFP64 = 1, kModeFP32 = 2 };
+
+template <typename VI>
+struct SolveParams {
+  WalkGraph g;
+  const float* dinv;
+  // problem (column c of this launch: s + c*ld)
+  const double* s;
+  int64_t ld;
+  double* z_out;  // nullable, same layout as s
+  double* quant;  // [K][5]
+  double* resid;  // [K]
+  int* status;    // [0] err bits, [1] iterations, [2] refinements
+  // row-major n x K workspace
+  double* sbar;
+  double* q;
+  double* t64;
+  VI* x;
+  VI* r;
+  VI* u;
+  VI* p;
+  VI* d;
+  VI* t;
+  int32_t* wc_row;
+  VI* wc_val;
+  double* wc_val64;
+  double* part;  // [gridDim][NSLOT][K]
+  Barrier* bar;
+  // options
+  double tol;
+  double inner_tol;
+  int max_iter;
+  int max_refine;
+  int mode;
+};
+
+// Grid-wide barrier with a bounded wait.  Returns false once any block has
+// given up (error bit kErrTimeout), after which every later barrier returns
+// at once so that all blocks leave the kernel.
+__device__ __forceinline__ bool grid_sync(Barrier* bar, int* status) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = (ld_volatile_i32(status) & kErrTimeout) == 0;
+    if (gridDim.x > 1 && ok) {
+      const unsigned gen = ld_acquire_u32(&bar->gen);
+      __threadfence();
+      const unsigned arrived = atomicAdd(&bar->count, 1u);
+      if (arrived == gridDim.x - 1) {
+        atomicExch(&bar->count, 0u);
+        __threadfence();
+        atomicAdd(&bar->gen, 1u);
+      } else {
+        const uint64_t t0 = global_ns();
+        unsigned spins = 0;
+        while (ld_acquire_u32(&bar->gen) == gen) {
+          if ((++spins & 255u) == 0) {
+            if ((ld_volatile_i32(status) & kErrTimeout) || global_ns() - t0 > kBarrierTimeoutNs) {
+              atomicOr(status, kErrTimeout);
+              ok = 0;
+              break;
+            }
+          }
+        }
+      }
+      __threadfence();
+    }
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// Block-level sums of NS per-thread values (thread column c = tid % K),
+// stored as this block's partials for the given slots.
+template <int K, int NS>
+__device__ __forceinline__ void block_store(const double (&v)[NS], const int (&slots)[NS],
+                                            double* part, double* red /*[NS][kWarps][K]*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    double x = v[j];
+#pragma unroll
+    for (int off = 16; off >= K; off >>= 1) x += __shfl_xor_sync(kFull, x, off);
+    if (lane < K) red[(j * kWarps + warp) * K + lane] = x;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NS * K; e += kThreads) {
+    const int j = e / K, c = e % K;
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += red[(j * kWarps + w) * K + c];
+    part[((int64_t)blockIdx.x * NSLOT + slots[j]) * K + c] = s;
+  }
+  __syncthreads();
+}
+
+// After a barrier: res[slot][c] = sum over blocks of the partials, in block
+// order, identically in every block.
+template <int K, int NS>
+__device__ __forceinline__ void grid_reduce(const int (&slots)[NS], const double* part,
+                                            double* res /*[NSLOT][K]*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = warp; e < NS * K; e += kWarps) {
+    const int slot = slots[e / K], c = e % K;
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&part[((int64_t)b * NSLOT + slot) * K + c]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+    if (lane == 0) res[slot * K + c] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+template <typename VI, int K>
+__global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams<VI> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileSmem* tsm = reinterpret_cast<TileSmem*>(smem_raw);
+  __shared__ double red[7 * kWarps * K];
+  __shared__ double res[NSLOT * K];
+  __shared__ double alpha[K], beta[K], gam_prev[K], alpha_prev[K], rr_goal[K], mu[K], bb[K];
+  __shared__ int active[K], first[K], done[K], inner_ok[K];
+  __shared__ int ctl_any_active, ctl_stop;
+
+  const int warp = threadIdx.x >> 5;
+  const int64_t n = P.g.n;
+  const int64_t NK = n * K;
+  const int64_t gtid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const int64_t gstride = (int64_t)gridDim.x * kThreads;
+  const int c = threadIdx.x % K;
+  const int64_t wg = (int64_t)blockIdx.x * kWarps + warp;
+  TileSmem* my_tsm = tsm + warp;
+  int* status = P.status;
+  const bool fp32_mode = P.mode == kModeFP32;
+
+  // ---------------------------------------------------------------- setup
+  {
+    double acc = 0.0;
+    for (int64_t idx = gtid; idx < NK; idx += gstride) acc += P.s[(int64_t)c * P.ld + idx / K];
+    const double v[1] = {acc};
+    const int sl[1] = {S_SUM};
+    block_store<K, 1>(v, sl, P.part, red);
+  }
+  if (!grid_sync(P.bar, status)) return;
+  {
+    const int sl[1] = {S_SUM};
+    grid_reduce<K, 1>(sl, P.part, res);
+    if (threadIdx.x < K) {
+      mu[threadIdx.x] = res[S_SUM * K + threadIdx.x] / (double)n;
+      done[threadIdx.x] = 0;
+    }
+    __syncthreads();
+  }
+
+  int iters = 0, refines = 0;
+  bool init = true;
+  while (true) {
+    // ------------------------------------------------ float64 residual pass
+    // r64 = s_bar - q - t64 (t64 = off-diagonal part of L q, from the walk)
+    // plus the quantity partials and the start of the next inner solve.
+    {
+      double a_rr64 = 0, a_p = 0, a_c = 0, a_ci = 0, a_bb = 0, a_gam = 0, a_rr = 0, a_uu = 0;
+      const double m = mu[c];
+      for (int64_t idx = gtid; idx < NK; idx += gstride) {
+        const int64_t i = idx / K;
+        double sb, qv, lq;
+        if (init) {
+          sb = P.s[(int64_t)c * P.ld + i] - m;
+          P.sbar[idx] = sb;
+          P.q[idx] = 0.0;
+          qv = 0.0;
+          lq = 0.0;
+          a_bb += sb * sb;
+        } else {
+          sb = P.sbar[idx];
+          qv = P.q[idx];
+          lq = row_total<double, K>(i, P.t64[idx], P.g.row_ptr, P.wc_val64, P.g.tiles_per_warp, c);
+        }
+        const double r64 = sb - qv - lq;
+        a_rr64 += r64 * r64;
+        a_p += qv * qv;
+        a_c += (qv + m) * (qv + m);
+        a_ci += (sb - qv) * (sb - qv);
+        const VI rv = (VI)r64;
+        const VI uv = P.dinv[i] * rv;
+        P.x[idx] = VI(0);
+        P.r[idx] = rv;
+        P.u[idx] = uv;
+        a_gam += (double)(rv * uv);
+        a_rr += (double)(rv * rv);
+        a_uu += (double)(uv * uv);
+      }
+      const double v[7] = {a_rr64, a_p, a_c, a_ci, a_gam, a_rr, a_uu};
+      const int sl[7] = {S_RR64, S_P, S_C, S_CI, S_GAM, S_RR, S_UU};
+      block_store<K, 7>(v, sl, P.part, red);
+      if (init) {
+        const double vb[1] = {a_bb};
+        const int sb[1] = {S_BB};
+        block_store<K, 1>(vb, sb, P.part, red);
+      }
+    }
+    if (!grid_sync(P.bar, status)) return;
+    {
+      const int sl[7] = {S_RR64, S_P, S_C, S_CI, S_GAM, S_RR, S_UU};
+      grid_reduce<K, 7>(sl, P.part, res);
+      if (init) {
+        const int sb[1] = {S_BB};
+        grid_reduce<K, 1>(sb, P.part, res);
+      } else {
+        const int sd[1] = {S_D};
+        grid_reduce<K, 1>(sd, P.part, res);
+      }
+    }
+    if (threadIdx.x == 0) ctl_stop = 0;
+    __syncthreads();
+    if (threadIdx.x < K) {
+      const int cc = threadIdx.x;
+      if (init) bb[cc] = res[S_BB * K + cc];
+      const double rr64 = res[S_RR64 * K + cc];
+      const double rel = bb[cc] > 0.0 ? sqrt(rr64 / bb[cc]) : 0.0;
+      if (!finite(rr64)) atomicOr(status, kErrNumeric);
+      // quantities of the current iterate (final after the last pass)
+      if (blockIdx.x == 0) {
+        const double D = init ? 0.0 : 0.5 * res[S_D * K + cc];
+        const double C = res[S_C * K + cc];
+        P.quant[cc * 5 + 0] = res[S_CI * K + cc];
+        P.quant[cc * 5 + 1] = D;
+        P.quant[cc * 5 + 2] = res[S_P * K + cc];
+        P.quant[cc * 5 + 3] = C;
+        P.quant[cc * 5 + 4] = D + C;
+        P.resid[cc] = rel;
+      }
+      bool conv = (bb[cc] == 0.0) || (rel <= P.tol);
+      if (fp32_mode && !init) conv = inner_ok[cc] || bb[cc] == 0.0;  // one inner solve only
+      if (!done[cc] && conv) done[cc] = 1;
+      // next inner solve for columns not done
+      const double rr = res[S_RR * K + cc];
+      double goal = P.inner_tol;
+      const double need = (rr64 > 0.0) ? 0.5 * P.tol * sqrt(bb[cc] / rr64) : 1.0;
+      if (P.mode == kModeFP64) goal = need;
+      else if (need > goal) goal = need;
+      if (fp32_mode) goal = P.tol;
+      rr_goal[cc] = goal * goal * rr;
+      active[cc] = !done[cc] && rr > rr_goal[cc];
+      inner_ok[cc] = !active[cc];
+      first[cc] = 1;
+    }
+    __syncthreads();
+    if (!init) ++refines;
+    if (threadIdx.x == 0) {
+      int all_done = 1, any = 0;
+      for (int j = 0; j < K; ++j) {
+        all_done &= done[j];
+        any |= active[j];
+      }
+      int stop = all_done || (ld_volatile_i32(status) & (kErrNumeric | kErrTimeout));
+      if (!init && refines >= P.max_refine) stop = 1;
+      if (!init && fp32_mode) stop = 1;
+      if (iters >= P.max_iter) stop = 1;
+      ctl_stop = stop;
+      ctl_any_active = any;
+    }
+    __syncthreads();
+    init = false;
+    if (ctl_stop) break;
+
+    // ------------------------------------------------------ inner PCG loop
+    while (ctl_any_active && iters < P.max_iter) {
+      // SpMV walk: t = off-diagonal part of (I + L) u, and the edge part of
+      // (u, (I+L) u).
+      {
+        const VI quad = walk_tiles<VI, K, kLap>(P.g, P.u, P.t, P.wc_row, P.wc_val, wg, my_tsm);
+        const double v[1] = {(double)quad};
+        const int sl[1] = {S_EQ};
+        block_store<K, 1>(v, sl, P.part, red);
+      }
+      if (!grid_sync(P.bar, status)) return;
+      {
+        const int sl[1] = {S_EQ};
+        grid_reduce<K, 1>(sl, P.part, res);
+      }
+      if (threadIdx.x < K) {
+        const int cc = threadIdx.x;
+        if (active[cc]) {
+          const double gam = res[S_GAM * K + cc];
+          // (u, (I+L) u) = u^T u + u^T L u, u^T L u = 1/2 sum over CSR entries
+          const double delta = res[S_UU * K + cc] + 0.5 * res[S_EQ * K + cc];
+          double a, b;
+          if (first[cc]) {
+            b = 0.0;
+            a = gam / delta;
+          } else {
+            b = gam / gam_prev[cc];
+            a = gam / (delta - b * gam / alpha_prev[cc]);
+          }
+          if (!finite(a) || !finite(b) || gam == 0.0) {
+            if (!(gam == 0.0)) atomicOr(status, kErrNumeric);
+            a = 0.0;
+            b = 0.0;
+            active[cc] = 0;
+          }
+          alpha[cc] = a;
+          beta[cc] = b;
+          gam_prev[cc] = gam;
+          alpha_prev[cc] = a;
+        } else {
+          alpha[cc] = 0.0;
+          beta[cc] = 0.0;
+        }
+      }
+      __syncthreads();
+      // vector update: p = u + beta p, d = w + beta d, x += alpha p,
+      // r -= alpha d, u = M r; partials (r,u), (r,r), (u,u).
+      {
+        double a_gam = 0, a_rr = 0, a_uu = 0;
+        const VI al = (VI)alpha[c], be = (VI)beta[c];
+        const bool fst = first[c] != 0;
+        VI l_gam = 0, l_rr = 0, l_uu = 0;
+        for (int64_t idx = gtid; idx < NK; idx += gstride) {
+          const int64_t i = idx / K;
+          const VI uv = P.u[idx];
+          const VI wv = uv + row_total<VI, K>(i, P.t[idx], P.g.row_ptr, P.wc_val, P.g.tiles_per_warp, c);
+          const VI pv = fst ? uv : uv + be * P.p[idx];
+          const VI dv = fst ? wv : wv + be * P.d[idx];
+          const VI xv = P.x[idx] + al * pv;
+          const VI rv = P.r[idx] - al * dv;
+          const VI un = P.dinv[i] * rv;
+          P.p[idx] = pv;
+          P.d[idx] = dv;
+          P.x[idx] = xv;
+          P.r[idx] = rv;
+          P.u[idx] = un;
+          l_gam += rv * un;
+          l_rr += rv * rv;
+          l_uu += un * un;
+        }
+        a_gam = (double)l_gam;
+        a_rr = (double)l_rr;
+        a_uu = (double)l_uu;
+        const double v[3] = {a_gam, a_rr, a_uu};
+        const int sl[3] = {S_GAM, S_RR, S_UU};
+        block_store<K, 3>(v, sl, P.part, red);
+      }
+      if (!grid_sync(P.bar, status)) return;
+      {
+        const int sl[3] = {S_GAM, S_RR, S_UU};
+        grid_reduce<K, 3>(sl, P.part, res);
+      }
+      ++iters;
+      if (threadIdx.x < K) {
+        const int cc = threadIdx.x;
+        first[cc] = 0;
+        const double rr = res[S_RR * K + cc];
+        if (!finite(rr)) {
+          atomicOr(status, kErrNumeric);
+          active[cc] = 0;
+        }
+        if (active[cc] && rr <= rr_goal[cc]) {
+          active[cc] = 0;
+          inner_ok[cc] = 1;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int any = 0;
+        for (int j = 0; j < K; ++j) any |= active[j];
+        if (ld_volatile_i32(status) & (kErrNumeric | kErrTimeout)) any = 0;
+        ctl_any_active = any;
+      }
+      __syncthreads();
+    }
+
+    // q += x (float64), then the residual walk t64 = L q and sum w (q_i-q_j)^2
+    for (int64_t idx = gtid; idx < NK; idx += gstride) P.q[idx] += (double)P.x[idx];
+    if (!grid_sync(P.bar, status)) return;
+    {
+      const double quad = walk_tiles<double, K, kLap>(P.g, P.q, P.t64, P.wc_row, P.wc_val64, wg, my_tsm);
+      const double v[1] = {quad};
+      const int sl[1] = {S_D};
+      block_store<K, 1>(v, sl, P.part, red);
+    }
+    if (!grid_sync(P.bar, status)) return;
+  }
+
+  // ---------------------------------------------------------------- output
+  if (P.z_out) {
+    for (int64_t idx = gtid; idx < NK; idx += gstride)
+      P.z_out[(int64_t)c * P.ld + idx / K] = P.q[idx] + mu[c];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int all_done = 1;
+    for (int j = 0; j < K; ++j) all_done &= done[j];
+    if (!all_done) atomicOr(status, kErrNotConverged);
+    status[1] = iters;
+    status[2] = refines;
+  }
+}
+
+// ------------------------------------------------------------------ host
+
+struct LaunchShape {
+  int blocks;
+  int64_t tiles_per_warp;
+};
+
+template <typename VI, int K>
+static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, const double* s,
+                            int64_t ld, double* z, double* quant, double* resid, int* status,
+                            char* ws, size_t ws_bytes, const fj_opts& o, int mode, int max_blocks) {
+  auto kern = k_solve<VI, K>;
+  const size_t dyn = kWarps * sizeof(TileSmem);
+  FJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  int per_sm = 0;
+  FJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, dyn));
+  if (per_sm < 1) {
+    set_error("solver kernel does not fit on an SM");
+    return FJ_ERR_CUDA;
+  }
+  const int64_t n = g->n;
+  // grid: enough blocks for the work, at most what is co-resident
+  const int64_t work = n * K + g->nnz * K;
+  int64_t want = (work + 8 * kThreads * 64 - 1) / (8 * kThreads * 64);
+  if (want < 1) want = 1;
+  int64_t cap = (int64_t)std::min(per_sm, kMaxBlocksPerSM) * num_sms;
+  if (max_blocks > 0 && cap > max_blocks) cap = max_blocks;
+  const int blocks = (int)std::min(want, cap);
+  const int64_t warps = (int64_t)blocks * kWarps;
+  const int64_t tpw = std::max<int64_t>(1, (g->n_tiles + warps - 1) / warps);
+
+  // carve the workspace
+  const int64_t NK = n * K;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = ws + off;
+    off += (bytes + 255) & ~size_t(255);
+    return (void*)p;
+  };
+  SolveParams<VI> P;
+  P.g = WalkGraph{g->row_ptr, g->col, g->val, g->tile_row, n, g->nnz, g->n_tiles, tpw};
+  P.dinv = g->dinv;
+  P.s = s;
+  P.ld = ld;
+  P.z_out = z;
+  P.quant = quant;
+  P.resid = resid;
+  P.status = status;
+  P.sbar = (double*)take(NK * 8);
+  P.q = (double*)take(NK * 8);
+  P.t64 = (double*)take(NK * 8);
+  P.x = (VI*)take(NK * sizeof(VI));
+  P.r = (VI*)take(NK * sizeof(VI));
+  P.u = (VI*)take(NK * sizeof(VI));
+  P.p = (VI*)take(NK * sizeof(VI));
+  P.d = (VI*)take(NK * sizeof(VI));
+  P.t = (VI*)take(NK * sizeof(VI));
+  P.wc_row = (int32_t*)take(warps * 4);
+  P.wc_val = (VI*)take(warps * K * sizeof(VI));
+  P.wc_val64 = (double*)take(warps * K * 8);
+  P.part = (double*)take((size_t)blocks * NSLOT * K * 8);
+  P.bar = (Barrier*)take(sizeof(Barrier));
+  if (off > ws_bytes) {
+    set_error("internal: workspace too small (%zu > %zu)", off, ws_bytes);
+    return FJ_ERR_OOM;
+  }
+  P.tol = o.tol;
+  P.inner_tol = o.inner_tol;
+  P.max_iter = o.max_iter;
+  P.max_refine = o.max_refine;
+  P.mode = mode;
+  FJ_CUDA(cudaMemsetAsync(P.bar, 0, sizeof(Barrier), st));
+  void* args[] = {&P};
+  FJ_CUDA(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(kThreads), args, dyn, st));
+  return FJ_OK;
+}
+
+}  // namespace fj
+
+using namespace fj;
+
+// Workspace bytes one launch of K columns needs.
+size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms) {
+  const int64_t NK = g->n * (int64_t)K;
+  const int64_t blocks = (int64_t)num_sms * kMaxBlocksPerSM;
+  const int64_t warps = blocks * kWarps;
+  size_t b = 0;
+  auto add = [&](size_t x) { b += (x + 255) & ~size_t(255); };
+  add(NK * 8);
+  add(NK * 8);
+  add(NK * 8);
+  for (int i = 0; i < 6; ++i) add(NK * inner_bytes);
+  add(warps * 4);
+  add(warps * K * inner_bytes);
+  add(warps * K * 8);
+  add((size_t)blocks * NSLOT * K * 8);
+  add(sizeof(Barrier));
+  return b;
+}
+
+// Runs the solve for columns [0, k) of s (column-major, leading dim n, all
+// device pointers) in launches of K = 32, 16, ..., 1 columns.
+// quant: device [k][5]; resid: device [k]; status: device int[3 * launches].
+fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k,
+                          const double* s, double* z, double* quant, double* resid, int* status,
+                          char* ws, size_t ws_bytes, const fj_opts& o, int* launches_out,
+                          int max_blocks) {
+  int mode = o.precision == FJ_PREC_FP64 ? kModeFP64 : (o.precision == FJ_PREC_FP32 ? kModeFP32 : kModeMixed);
+  int col = 0, li = 0;
+  while (col < k) {
+    const int left = k - col;
+    int K = 32;
+    while (K > left) K >>= 1;
+    const double* sc = s + (int64_t)col * g->n;
+    double* zc = z ? z + (int64_t)col * g->n : nullptr;
+    double* qc = quant + (int64_t)col * 5;
+    double* rc = resid + col;
+    int* stc = status + 3 * li;
+    fj_status rcode;
+#define FJ_LAUNCH(KK)                                                                                  \
+  if (mode == kModeFP64)                                                                               \
+    rcode = launch_one<double, KK>(g, st, num_sms, sc, g->n, zc, qc, rc, stc, ws, ws_bytes, o, mode,   \
+                                   max_blocks);                                                        \
+  else                                                                                                 \
+    rcode = launch_one<float, KK>(g, st, num_sms, sc, g->n, zc, qc, rc, stc, ws, ws_bytes, o, mode,    \
+                                  max_blocks);
+    switch (K) {
+      case 32: FJ_LAUNCH(32) break;
+      case 16: FJ_LAUNCH(16) break;
+      case 8: FJ_LAUNCH(8) break;
+      case 4: FJ_LAUNCH(4) break;
+      case 2: FJ_LAUNCH(2) break;
+      default: FJ_LAUNCH(1) break;
+    }
+#undef FJ_LAUNCH
+    if (rcode != FJ_OK) return rcode;
+    col += K;
+    ++li;
+  }
+  *launches_out = li;
+  return FJ_OK;
+}

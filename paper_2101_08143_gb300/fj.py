@@ -1,0 +1,274 @@
+"""Python binding of libfj (include/fj.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+converts numpy arrays / torch CUDA tensors into pointers and sizes.  Importing
+it loads libfj.so and raises if the library is missing: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FJ_OK = 0
+FJ_PENDING = 1
+FJ_ERR_ARG = -1
+FJ_ERR_GRAPH = -2
+FJ_ERR_OOM = -3
+FJ_ERR_ADMIT = -4
+FJ_ERR_NOT_CONVERGED = -5
+FJ_ERR_NUMERIC = -6
+FJ_ERR_TIMEOUT = -7
+FJ_ERR_CUDA = -8
+FJ_ERR_TICKET = -9
+
+FJ_HOST_PTRS = 0
+FJ_DEVICE_PTRS = 1
+
+PREC_MIXED = 0
+PREC_FP64 = 1
+PREC_FP32 = 2
+
+QUANTITY_NAMES = ("C_I", "D", "P", "C", "I_dc")
+
+
+class FJError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fj error {code}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("max_refine", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("device_ms", ctypes.c_double),
+                ("status", ctypes.c_int32), ("columns", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Quant(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_double) for name in QUANTITY_NAMES]
+
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "fj_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "fj_last_error": (ctypes.c_char_p, []),
+    "fj_version": (ctypes.c_char_p, []),
+    "fj_create": (ctypes.c_int32, [ctypes.c_int, ctypes.POINTER(_P)]),
+    "fj_destroy": (ctypes.c_int32, [_P]),
+    "fj_set_stream": (ctypes.c_int32, [_P, _P]),
+    "fj_set_max_blocks": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "fj_graph_upload": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
+                                         ctypes.c_uint32, ctypes.POINTER(_P)]),
+    "fj_graph_free": (ctypes.c_int32, [_P, _P]),
+    "fj_graph_stats": (ctypes.c_int32, [_P, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "fj_solve_ex": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P,
+                                     ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
+    "fj_solve": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P,
+                                  ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
+    "fj_quantities": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P,
+                                       ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libfj.so (building it first if needed).  Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise FJError(FJ_ERR_CUDA, f"libfj.so not found at {path}")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code, what=""):
+    if code != FJ_OK:
+        msg = load().fj_last_error().decode()
+        raise FJError(code, f"{what}: {msg}" if what else msg)
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load().fj_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _is_torch_cuda(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+class Graph:
+    def __init__(self, ctx: "Context", handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    def stats(self):
+        n = ctypes.c_int64()
+        nnz = ctypes.c_int64()
+        wt = ctypes.c_int32()
+        _check(load().fj_graph_stats(self.handle, ctypes.byref(n), ctypes.byref(nnz),
+                                     ctypes.byref(wt)), "fj_graph_stats")
+        return {"n": n.value, "nnz": nnz.value, "weighted": bool(wt.value)}
+
+    def free(self):
+        if self.handle:
+            _check(load().fj_graph_free(self.ctx.handle, self.handle), "fj_graph_free")
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+
+class Context:
+    """A libfj context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = _P()
+        _check(lib.fj_create(device, ctypes.byref(h)), "fj_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            load().fj_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream_ptr: int | None):
+        _check(load().fj_set_stream(self.handle, _P(stream_ptr or 0)), "fj_set_stream")
+
+    def set_max_blocks(self, nblocks: int):
+        _check(load().fj_set_max_blocks(self.handle, int(nblocks)), "fj_set_max_blocks")
+
+    # ------------------------------------------------------------- graphs
+    def upload(self, n, src, dst, w=None) -> Graph:
+        """Edge list -> device CSR.  numpy arrays (host) or torch CUDA tensors
+        (device); w=None means unit weights."""
+        h = _P()
+        if _is_torch_cuda(src):
+            m = int(src.numel())
+            args = (src.data_ptr(), dst.data_ptr(), w.data_ptr() if w is not None else None)
+            flags = FJ_DEVICE_PTRS
+            keep = None
+        else:
+            src = np.ascontiguousarray(src, dtype=np.int32)
+            dst = np.ascontiguousarray(dst, dtype=np.int32)
+            w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+            m = int(src.shape[0])
+            keep = (src, dst, w)
+            args = (src.ctypes.data, dst.ctypes.data, None if w is None else w.ctypes.data)
+            flags = FJ_HOST_PTRS
+        rc = load().fj_graph_upload(self.handle, int(n), m, _P(args[0]), _P(args[1]),
+                                    _P(args[2]), flags, ctypes.byref(h))
+        del keep
+        _check(rc, "fj_graph_upload")
+        return Graph(self, h)
+
+    def upload_edges(self, edges) -> Graph:
+        """Upload a synth.EdgeList."""
+        return self.upload(edges.n, edges.src, edges.dst, edges.w)
+
+    # -------------------------------------------------------------- solve
+    def solve(self, graph: Graph, s, want_z=True, want_quant=True, opts: Opts | None = None,
+              z_out=None, raise_on_error=True):
+        """Solve (I + L) z = s for the columns of s.
+
+        s: numpy float64 (n,) or (n, k) [host], or a torch float64 CUDA tensor
+        of shape (k, n) / (n,) whose rows are the columns (column-major n x k
+        memory) [device].  Returns (z, quantities, info); z is a numpy (n, k)
+        array for host input, or the z_out / new torch tensor for device input.
+        """
+        lib = load()
+        o = Opts() if opts is None else opts
+        if opts is None:
+            lib.fj_default_opts(ctypes.byref(o))
+        else:
+            o = Opts(opts.tol, opts.inner_tol, opts.precision, opts.max_iter,
+                     opts.max_refine, opts.flags)
+        n = graph.stats()["n"]
+        if _is_torch_cuda(s):
+            import torch
+            k = 1 if s.dim() == 1 else int(s.shape[0])
+            if not s.is_contiguous() or s.dtype != torch.float64 or s.numel() != n * k:
+                raise ValueError("device s must be contiguous float64 with n*k elements")
+            z = None
+            if want_z:
+                z = z_out if z_out is not None else torch.empty_like(s)
+            sp, zp = s.data_ptr(), (z.data_ptr() if z is not None else None)
+            o.flags = FJ_DEVICE_PTRS
+            keep = None
+        else:
+            s = np.asarray(s, dtype=np.float64)
+            squeeze = s.ndim == 1
+            s2 = s.reshape(n, -1)
+            k = s2.shape[1]
+            sf = np.asfortranarray(s2)
+            z = np.empty((n, k), dtype=np.float64, order="F") if want_z else None
+            sp = sf.ctypes.data
+            zp = z.ctypes.data if z is not None else None
+            o.flags = FJ_HOST_PTRS
+            keep = sf
+        quant = (Quant * k)() if want_quant else None
+        info = Info()
+        rc = lib.fj_solve_ex(self.handle, graph.handle, k, _P(sp), _P(zp),
+                             ctypes.cast(quant, _P) if quant is not None else None,
+                             ctypes.byref(o), ctypes.byref(info))
+        del keep
+        if raise_on_error:
+            _check(rc, "fj_solve_ex")
+        qs = None
+        if quant is not None:
+            qs = [{name: getattr(quant[j], name) for name in QUANTITY_NAMES} for j in range(k)]
+        if z is not None and not _is_torch_cuda(s) and squeeze:
+            z = z[:, 0]
+        d = info.as_dict()
+        d["rc"] = rc
+        return z, qs, d
+
+    def quantities(self, graph: Graph, s, opts: Opts | None = None):
+        _, q, info = self.solve(graph, s, want_z=False, want_quant=True, opts=opts)
+        return q, info
+
+
+def version() -> str:
+    return load().fj_version().decode()

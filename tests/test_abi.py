@@ -1,0 +1,53 @@
+"""The C-ABI library builds, loads, and exports every symbol of include/fj.h.
+No compute call is made here (this file runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2101_08143_gb300 import fj
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(fj_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_symbols_exported():
+    lib = fj.load()
+    names = _declared_symbols()
+    assert "fj_solve" in names and "fj_graph_upload" in names
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_defaults():
+    assert "sm_103a" in fj.version()
+    o = fj.default_opts()
+    assert o.tol == 1e-10 and o.precision == fj.PREC_MIXED and o.max_iter > 0
+
+
+def test_null_arguments_are_rejected_without_a_device():
+    lib = fj.load()
+    assert lib.fj_solve_ex(None, None, 1, None, None, None, None, None) == fj.FJ_ERR_ARG
+    assert b"non-NULL" in lib.fj_last_error()
+    assert lib.fj_graph_stats(None, None, None, None) == fj.FJ_ERR_ARG
+    assert lib.fj_set_max_blocks(None, 3) == fj.FJ_ERR_ARG
+    assert lib.fj_destroy(None) == fj.FJ_OK
+
+
+def test_built_for_sm_103a():
+    from paper_2101_08143_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+    assert os.path.exists(build.LIB)

@@ -1,0 +1,231 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative error per quantity, the paper's sigma = |rho - rho~|/rho):
+  mixed (float32 inner + float64 refinement) and float64 modes: 1e-6
+  pure float32 mode: 1e-3
+"""
+import numpy as np
+import pytest
+
+import oracle.fj_oracle as fo
+from paper_2101_08143_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-6, 1: 1e-6, 2: 1e-3}  # by precision mode
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_08143_gb300 import fj
+    c = fj.Context(0)
+    yield c
+    c.close()
+
+
+def _floor(s):
+    return 1e-12 * float(np.sum(np.asarray(s) ** 2))
+
+
+def _check_quantities(gq, oq, s, rtol):
+    for name in fo.QUANTITY_NAMES:
+        err = fo.relative_error(oq[name], gq[name], floor=_floor(s))
+        assert err <= rtol, (name, gq[name], oq[name], err)
+
+
+def _oracle(g, s, tol=1e-12):
+    s = np.asarray(s, dtype=np.float64).reshape(g.n, -1)
+    z = fo.solve(g.n, g.src, g.dst, g.w, s, tol=tol).reshape(g.n, -1)
+    q = [fo.quantities_from_z(g.n, g.src, g.dst, g.w, s[:, j], z[:, j]) for j in range(s.shape[1])]
+    return z, q
+
+
+def test_p5_forest_matrix(ctx):
+    from paper_2101_08143_gb300 import fj
+    g = synth.path_graph(5)
+    with ctx.upload_edges(g) as dg:
+        om, _, info = ctx.solve(dg, np.eye(5), opts=fj.default_opts(tol=1e-13))
+    expect = fo.forest_matrix(5, g.src, g.dst, g.w)
+    np.testing.assert_allclose(om, expect, atol=1e-12)
+    assert abs(om[0, 1] * 55 - 13) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_erdos_renyi_2k(ctx, prec):
+    """n = 2,000 ER graph, average degree 10, unit weights, s ~ U[0,1]."""
+    from paper_2101_08143_gb300 import fj
+    spec = synth.WORKLOADS["er_n2k_d10"]
+    g = synth.make_graph(spec)
+    s = synth.make_opinions(spec, g.n)[:, 0]
+    zo, qo = _oracle(g, s)
+    with ctx.upload_edges(g) as dg:
+        assert dg.stats() == {"n": 2000, "nnz": 20000, "weighted": False}
+        z, q, info = ctx.solve(dg, s, opts=fj.default_opts(precision=prec, tol=1e-10 if prec != 2 else 1e-6))
+    _check_quantities(q[0], qo[0], s, TOL[prec])
+    ztol = 1e-8 if prec != 2 else 1e-4
+    np.testing.assert_allclose(z, zo[:, 0], atol=ztol)
+    if prec != 2:
+        assert info["rel_residual"] <= 1e-10
+    assert info["iterations"] > 0
+
+
+@pytest.mark.parametrize("n,m,weighted,seed", [(300, 900, True, 1), (1000, 20000, True, 2),
+                                               (4097, 9000, False, 3), (12345, 60000, True, 4)])
+def test_random_graphs_several_tiles(ctx, n, m, weighted, seed):
+    g = synth.erdos_renyi(n, m, seed=seed, weighted=weighted)
+    s = synth.opinions_uniform(n, 1, seed)[:, 0]
+    zo, qo = _oracle(g, s)
+    with ctx.upload_edges(g) as dg:
+        z, q, _ = ctx.solve(dg, s)
+    _check_quantities(q[0], qo[0], s, 1e-6)
+    np.testing.assert_allclose(z, zo[:, 0], atol=1e-8)
+
+
+@pytest.mark.parametrize("k", [2, 3, 7, 33])
+def test_multi_rhs(ctx, k):
+    """k opinion vectors in one call (launches of 32/16/8/4/2/1 columns)."""
+    g = synth.chung_lu(5000, 20000, 2.3, seed=11, weighted=True)
+    s = synth.opinions_batch_mix(g.n, k, 5)
+    zo, qo = _oracle(g, s)
+    with ctx.upload_edges(g) as dg:
+        z, q, _ = ctx.solve(dg, s)
+    for j in range(k):
+        _check_quantities(q[j], qo[j], s[:, j], 1e-6)
+    np.testing.assert_allclose(z, zo, atol=1e-8)
+
+
+def test_chung_lu_hubs(ctx):
+    """Power-law graph whose hub rows span many tiles and warps."""
+    g = synth.chung_lu(60_000, 300_000, 2.1, seed=7, weighted=True)
+    s = synth.opinions_polarized(g.n, 1, 3)[:, 0]
+    zo, qo = _oracle(g, s)
+    with ctx.upload_edges(g) as dg:
+        z, q, info = ctx.solve(dg, s)
+    _check_quantities(q[0], qo[0], s, 1e-6)
+    np.testing.assert_allclose(z, zo[:, 0], atol=1e-8)
+
+
+@pytest.mark.parametrize("blocks", [1, 2, 5])
+def test_launch_shapes_agree(ctx, blocks):
+    """Small persistent grids (down to one block) give the same results."""
+    g = synth.chung_lu(20_000, 80_000, 2.3, seed=8, weighted=True)
+    s = synth.opinions_uniform(g.n, 1, 4)[:, 0]
+    zo, qo = _oracle(g, s)
+    ctx.set_max_blocks(blocks)
+    try:
+        with ctx.upload_edges(g) as dg:
+            z, q, _ = ctx.solve(dg, s)
+    finally:
+        ctx.set_max_blocks(0)
+    _check_quantities(q[0], qo[0], s, 1e-6)
+    np.testing.assert_allclose(z, zo[:, 0], atol=1e-8)
+
+
+def test_deterministic_bits(ctx):
+    g = synth.chung_lu(30_000, 120_000, 2.2, seed=9, weighted=True)
+    s = synth.opinions_uniform(g.n, 2, 6)
+    with ctx.upload_edges(g) as dg:
+        z1, q1, _ = ctx.solve(dg, s)
+        z2, q2, _ = ctx.solve(dg, s)
+    with ctx.upload_edges(g) as dg2:
+        z3, q3, _ = ctx.solve(dg2, s)
+    assert np.array_equal(z1, z2) and np.array_equal(z1, z3)
+    assert q1 == q2 == q3
+
+
+# ------------------------------------------------------------ edge cases
+
+def test_edgeless_graph(ctx):
+    g = synth.edgeless(1000)
+    s = synth.opinions_uniform(1000, 1, 1)[:, 0]
+    with ctx.upload_edges(g) as dg:
+        z, q, _ = ctx.solve(dg, s)
+    np.testing.assert_allclose(z, s, atol=1e-14)
+    assert q[0]["C_I"] < 1e-20 and q[0]["D"] == 0.0
+    assert q[0]["C"] == pytest.approx(float(np.sum(s ** 2)), rel=1e-13)
+
+
+def test_single_node(ctx):
+    with ctx.upload(1, np.zeros(0, np.int32), np.zeros(0, np.int32)) as dg:
+        z, q, _ = ctx.solve(dg, np.array([0.7]))
+    assert z[0] == pytest.approx(0.7)
+    assert q[0]["P"] == 0.0 and q[0]["C"] == pytest.approx(0.49)
+
+
+def test_constant_opinions(ctx):
+    g = synth.erdos_renyi(3000, 12000, seed=2, weighted=True)
+    s = np.full(3000, 0.25)
+    with ctx.upload_edges(g) as dg:
+        z, q, info = ctx.solve(dg, s)
+    np.testing.assert_allclose(z, 0.25, atol=1e-15)
+    assert q[0]["P"] < 1e-25 and q[0]["D"] < 1e-25 and q[0]["C_I"] < 1e-25
+
+
+def test_self_loops_and_parallel_edges(ctx):
+    """Self-loops vanish, repeated pairs add their weights."""
+    src = np.array([0, 1, 0, 2, 2, 3, 3], np.int32)
+    dst = np.array([1, 2, 1, 2, 3, 3, 0], np.int32)
+    w = np.array([0.5, 1.0, 0.25, 9.0, 2.0, 4.0, 0.125], np.float32)
+    s = np.array([0.9, 0.1, 0.4, 0.7])
+    expect = fo.solve_dense(4, src, dst, w, s)
+    with ctx.upload(4, src, dst, w) as dg:
+        assert dg.stats()["nnz"] == 10
+        z, _, _ = ctx.solve(dg, s)
+    np.testing.assert_allclose(z, expect, atol=1e-12)
+
+
+def test_disconnected_components(ctx):
+    a = synth.erdos_renyi(500, 2000, seed=3, weighted=True)
+    src = np.concatenate([a.src, a.src + 500])
+    dst = np.concatenate([a.dst, a.dst + 500])
+    w = np.concatenate([a.w, a.w * 0.5])
+    s = synth.opinions_uniform(1000, 1, 2)[:, 0]
+    zo = fo.solve(1000, src, dst, w, s)
+    with ctx.upload(1000, src, dst, w) as dg:
+        z, _, _ = ctx.solve(dg, s)
+    np.testing.assert_allclose(z, zo, atol=1e-9)
+    assert z[:500].sum() == pytest.approx(s[:500].sum(), rel=1e-10)
+
+
+def test_bad_graphs_rejected(ctx):
+    from paper_2101_08143_gb300 import fj
+    with pytest.raises(fj.FJError) as e:
+        ctx.upload(3, np.array([0, 3], np.int32), np.array([1, 1], np.int32))
+    assert e.value.code == fj.FJ_ERR_GRAPH
+    with pytest.raises(fj.FJError) as e:
+        ctx.upload(3, np.array([0], np.int32), np.array([1], np.int32), np.array([0.0], np.float32))
+    assert e.value.code == fj.FJ_ERR_GRAPH
+    with pytest.raises(fj.FJError) as e:
+        ctx.upload(3, np.array([0], np.int32), np.array([1], np.int32), np.array([np.nan], np.float32))
+    assert e.value.code == fj.FJ_ERR_GRAPH
+    with pytest.raises(fj.FJError) as e:
+        ctx.upload(0, np.array([], np.int32), np.array([], np.int32))
+    assert e.value.code == fj.FJ_ERR_ARG
+
+
+def test_not_converged_reported(ctx):
+    from paper_2101_08143_gb300 import fj
+    g = synth.chung_lu(20_000, 80_000, 2.3, seed=8, weighted=True)
+    s = synth.opinions_uniform(g.n, 1, 4)[:, 0]
+    with ctx.upload_edges(g) as dg:
+        _, q, info = ctx.solve(dg, s, opts=fj.default_opts(max_iter=3), raise_on_error=False)
+    assert info["rc"] == fj.FJ_ERR_NOT_CONVERGED
+    assert info["iterations"] <= 3
+
+
+def test_device_pointers(ctx):
+    """s and z as torch CUDA tensors (column-major: shape (k, n))."""
+    import torch
+    g = synth.erdos_renyi(5000, 25000, seed=5, weighted=True)
+    s = synth.opinions_uniform(g.n, 3, 9)
+    zo, qo = _oracle(g, s)
+    sd = torch.from_numpy(np.ascontiguousarray(s.T)).cuda()
+    with ctx.upload(g.n, torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda(),
+                    torch.from_numpy(g.w).cuda()) as dg:
+        z, q, _ = ctx.solve(dg, sd)
+    np.testing.assert_allclose(z.cpu().numpy().T, zo, atol=1e-8)
+    for j in range(3):
+        _check_quantities(q[j], qo[j], s[:, j], 1e-6)
