@@ -1,0 +1,348 @@
+"""Benchmark of the FJ hot path on GB300.
+
+One step = the whole path on one synthetic problem already resident in HBM:
+graph ingest (edge list -> CSR of I + L), centring, the mixed-precision
+Jacobi-PCG solve of (I + L) q = s_bar to the workload's relative residual,
+and the five quantities plus z.  Default workload: Chung-Lu power-law graph,
+n = 1,000,000, m = 5,000,000 undirected edges, exponent 2.3, weights
+Uniform(0,1] float32, one opinion vector s ~ Uniform[0,1], float32 inner
+iterations with float64 refinement to relative residual 1e-8.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+# The oracle's numpy must run on one core so that the CPU figure is honest.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2101_08143_gb300 import synth  # noqa: E402
+
+METRIC = "solves/s and HBM GB/s (% of peak) of (I+L)z=s at 1e-6 rel err; p50/p99 latency"
+WORKLOAD = "cl_n1m_m5m_b2.3"
+TOL = 1e-8
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload_desc(spec, g, nnz=None):
+    d = {"workload": (f"chung-lu n={spec['n']:,} m={spec['m']:,} exponent={spec['exponent']} "
+                      f"w~U(0,1] f32, k={spec['k']} s~U[0,1], mixed PCG to rel. residual {TOL:g}"),
+         "n": g.n, "m": g.m, "k": spec["k"], "tol": TOL,
+         "step": "graph ingest + centring + solve + 5 quantities + z (inputs resident in HBM)",
+         "l2": "flushed (512 MiB write) before every timed step"}
+    if nnz is not None:
+        d["nnz"] = nnz
+    return d
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = None
+        self.device = device_index
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _bytes_per_launch(n, nnz, weighted, k, iters, refines):
+    """Algorithmic bytes of one solve launch: per inner iteration
+    4(n+1) + nnz (4 + 4 [weighted]) + 52 n k; per float64 refinement the graph
+    again plus 24 n k."""
+    graph = 4 * (n + 1) + nnz * (4 + (4 if weighted else 0))
+    return iters * (graph + 52 * n * k) + refines * (graph + 24 * n * k)
+
+
+def run_cpu_baseline(g, s, n_solves, tol=TOL):
+    import oracle.fj_oracle as fo
+    t0 = time.perf_counter()
+    for _ in range(n_solves):
+        fo.quantities(g.n, g.src, g.dst, g.w, s, tol=tol)
+    dt = time.perf_counter() - t0
+    return n_solves / dt, dt
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the arm's workload (host cores)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle.fj_oracle as fo
+    spec = synth.WORKLOADS[args.workload]
+    g = synth.make_graph(spec)
+    s = synth.make_opinions(spec, g.n)[:, 0]
+    for _ in range(args.warmup):  # warm-up: one operator application each
+        fo.apply_i_plus_l(g.n, g.src, g.dst, g.w, s)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        fo.quantities(g.n, g.src, g.dst, g.w, s, tol=TOL)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _workload_desc(spec, g),
+            "latency_ms": {"p50": 1000 * float(np.percentile(times, 50)),
+                           "p99": 1000 * float(np.percentile(times, 99))},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full oracle solves + quantities of the workload"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--cpu-solves", type=int, default=3, help="oracle solves in the CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}), flush=True)
+        return 1
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2101_08143_gb300 import fj
+
+    lib = fj.load()
+    spec = synth.WORKLOADS[args.workload]
+    g = synth.make_graph(spec)
+    k = spec["k"]
+    s_host = synth.make_opinions(spec, g.n)  # n x k, column-major
+    weighted = g.w is not None
+
+    ctx = fj.Context(local)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    dev = torch.device("cuda", local)
+    src_d = torch.from_numpy(g.src).to(dev)
+    dst_d = torch.from_numpy(g.dst).to(dev)
+    w_d = torch.from_numpy(g.w).to(dev) if weighted else None
+    s_d = torch.from_numpy(np.ascontiguousarray(s_host.T)).to(dev)  # (k, n) = column-major
+    z_d = torch.empty_like(s_d)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    opts = fj.default_opts(tol=TOL, precision=fj.PREC_MIXED)
+
+    def step():
+        gr = ctx.upload(g.n, src_d, dst_d, w_d)
+        _, q, info = ctx.solve(gr, s_d, opts=opts, z_out=z_d)
+        gr.free()
+        return q, info
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            q, info = step()
+        # graph statistics for the byte model
+        gr = ctx.upload(g.n, src_d, dst_d, w_d)
+        nnz = gr.stats()["nnz"]
+        gr.free()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    launches0 = lib.fj_kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    infos = []
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            q, info = step()
+            evs[i][1].record(stream)
+            infos.append(info)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = lib.fj_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * k / (total_ms / 1000.0)
+
+    # roofline of the solve kernel (one cooperative launch per step for k <= 32)
+    kern_ms = float(np.mean([i["device_ms"] for i in infos]))
+    iters = int(np.mean([i["iterations"] for i in infos]))
+    refines = int(np.mean([i["refinements"] for i in infos]))
+    algo = _bytes_per_launch(g.n, nnz, weighted, k, iters, refines)
+    achieved = algo / (kern_ms / 1000.0) / 1e9
+    peak, peak_kind = _peaks()
+
+    # solve-only rate on a resident graph (same opts), for context
+    with torch.cuda.stream(stream):
+        gr = ctx.upload(g.n, src_d, dst_d, w_d)
+        so = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.solve(gr, s_d, opts=opts, z_out=z_d)
+            b.record(stream)
+            so.append((a, b))
+        torch.cuda.synchronize()
+        solve_ms = [a.elapsed_time(b) for a, b in so]
+        gr.free()
+
+    # end to end through the public API with host buffers (pinned)
+    src_h = torch.from_numpy(g.src).pin_memory().numpy()
+    dst_h = torch.from_numpy(g.dst).pin_memory().numpy()
+    w_h = torch.from_numpy(g.w).pin_memory().numpy() if weighted else None
+    s_pin = torch.empty((k, g.n), dtype=torch.float64).pin_memory().numpy()
+    s_pin[:] = s_host.T
+    s_h = s_pin.T if k > 1 else s_pin.reshape(g.n)  # (n, k) column-major view
+    z_h = torch.empty((k, g.n), dtype=torch.float64).pin_memory().numpy().T
+    e2e_ms = []
+    for i in range(args.warmup + max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gr = ctx.upload(g.n, src_h, dst_h, w_h)
+        ctx.solve(gr, s_h, opts=opts, z_out=z_h)
+        gr.free()
+        if i >= args.warmup:
+            e2e_ms.append(1000 * (time.perf_counter() - t0))
+    e2e_total = float(sum(e2e_ms))
+    if dist:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_val = world * len(e2e_ms) * k / (e2e_total / 1000.0)
+    h2d = g.m * 4 * (3 if weighted else 2) + g.n * k * 8
+    d2h = g.n * k * 8 + k * 5 * 8
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": _workload_desc(spec, g, nnz),
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                           "p99": float(np.percentile(step_ms, 99))},
+            "solve_only": {"value": 1000.0 / float(np.mean(solve_ms)), "unit": "solves/s",
+                           "p50_ms": float(np.percentile(solve_ms, 50)),
+                           "p99_ms": float(np.percentile(solve_ms, 99)),
+                           "note": "resident graph, solve + quantities + z"},
+            "iterations": {"inner": iters, "refinements": refines,
+                           "rel_residual": max(i["rel_residual"] for i in infos)},
+            "roofline": {"kernel": "k_solve<float,1>", "bound": "hbm", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": f"{peak_kind} (hbm_gbs, burst copy)",
+                         "traffic": None, "algorithmic_bytes": algo,
+                         "kernel_ms": kern_ms},
+            "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "p50_ms": float(np.percentile(e2e_ms, 50))},
+            "gpu_launches": int(launches),
+            "gpu_launches_per_step": launches / args.steps,
+            "wall_s_timed": wall,
+            "clocks": clk,
+            "quantities": q[0],
+        }
+    ctx.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s0 = s_host[:, 0]
+        v, dt = run_cpu_baseline(g, s0, args.cpu_solves)
+        line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{args.cpu_solves} full oracle solves (FP64 CG to "
+                                          f"{TOL:g}) + quantities of the workload, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -112,6 +112,10 @@ void fj_default_opts(fj_opts* opts);
 /* Thread-local text of the last error raised on this thread ("" if none). */
 const char* fj_last_error(void);
 
+/* Number of CUDA kernels the library has launched in this process, over all
+ * contexts (a counter for measuring how much device work a call issues). */
+int64_t fj_kernel_launches(void);
+
 /* Library version string. */
 const char* fj_version(void);
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -29,6 +30,9 @@ fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32
 namespace fj {
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   char buf[512];
@@ -126,6 +130,8 @@ void fj_default_opts(fj_opts* o) {
 }
 
 const char* fj_last_error(void) { return g_last_error.c_str(); }
+
+int64_t fj_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 const char* fj_version(void) { return "fj-gb300 0.1 (sm_103a)"; }
 

@@ -1,17 +1,20 @@
-// fj_graph.cu - device construction of the CSR of I + L (Sec. 2.1).
+// fj_graph.cu - device construction of the graph of I + L (Sec. 2.1).
 //
 // Input: an undirected edge list (src, dst, w), each edge once.  Every edge
 // e = (u, v) yields two directed entries, (row u, col v) and (row v, col u),
 // numbered 2e and 2e+1.  A stable LSD radix sort of the 2m entries by row
-// id gives the CSR directly; inside a row, entries keep their input order,
-// so the CSR (and every sum over it) is the same bits on every upload.
-// Self-loops get the key n and sort past the last row, i.e. they are
-// dropped (b_e = e_i - e_i = 0 contributes nothing to L).
+// id gives a CSR whose rows keep the input order of their entries, so the
+// graph (and every sum over it) is the same bits on every upload.  Self-loops
+// get the key n and sort past the last row, i.e. they are dropped
+// (b_e = e_i - e_i = 0 contributes nothing to L).
 //
-// Then: row_ptr from the sorted keys, weighted degrees d_i by a merge-path
-// walk (balanced over hubs), dinv = 1 / (1 + d_i), and the merge-path tile
-// plan (row coordinate of every tile start) used by all later walks.
+// The nodes are then renumbered by decreasing degree (a stable radix sort of
+// saturated degree keys), the CSR is rewritten in that order, and the SpMV
+// layouts are derived from it: chunks of the long rows, sliced ELL for the
+// rest, the static work partition, the merge-path tile plan and the Jacobi
+// preconditioner 1 / (1 + d_i).
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "fj_internal.cuh"
@@ -152,80 +155,87 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
 
 // ------------------------------------------------------------------ scan
 
-__device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& total) {
-  // sh: kScanThreads/32 ints
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* sh, T& total) {
+  // sh: kScanThreads/32 values
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int x = v;
+  T x = v;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    const int y = __shfl_up_sync(kFull, x, off);
+    const T y = __shfl_up_sync(kFull, x, off);
     if (lane >= off) x += y;
   }
   if (lane == 31) sh[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    int s = (lane < kScanThreads / 32) ? sh[lane] : 0;
+    T s = (lane < kScanThreads / 32) ? sh[lane] : T(0);
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const int y = __shfl_up_sync(kFull, s, off);
+      const T y = __shfl_up_sync(kFull, s, off);
       if (lane >= off) s += y;
     }
     if (lane < kScanThreads / 32) sh[lane] = s;
   }
   __syncthreads();
   total = sh[kScanThreads / 32 - 1];
-  const int before = warp > 0 ? sh[warp - 1] : 0;
+  const T before = warp > 0 ? sh[warp - 1] : T(0);
   __syncthreads();
   return before + x - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* __restrict__ in, int64_t cnt,
-                                                              int32_t* __restrict__ sums) {
-  __shared__ int sh[kScanThreads / 32];
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* __restrict__ in, int64_t cnt,
+                                                              T* __restrict__ sums) {
+  __shared__ T sh[kScanThreads / 32];
   const int64_t base = (int64_t)blockIdx.x * kScanChunk;
-  int v = 0;
+  T v = 0;
   for (int i = 0; i < kScanItems; ++i) {
     const int64_t p = base + (int64_t)threadIdx.x * kScanItems + i;
     if (p < cnt) v += in[p];
   }
-  int total;
-  block_exclusive_scan(v, sh, total);
+  T total;
+  block_exclusive_scan<T>(v, sh, total);
   if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(int32_t* __restrict__ data, int64_t cnt,
-                                                             const int32_t* __restrict__ offs) {
-  __shared__ int sh[kScanThreads / 32];
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(T* __restrict__ data, int64_t cnt,
+                                                             const T* __restrict__ offs) {
+  __shared__ T sh[kScanThreads / 32];
   const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
-  int vals[kScanItems];
-  int v = 0;
+  T vals[kScanItems];
+  T v = 0;
   for (int i = 0; i < kScanItems; ++i) {
-    vals[i] = (base + i < cnt) ? data[base + i] : 0;
+    vals[i] = (base + i < cnt) ? data[base + i] : T(0);
     v += vals[i];
   }
-  int total;
-  int run = block_exclusive_scan(v, sh, total) + (offs ? offs[blockIdx.x] : 0);
+  T total;
+  T run = block_exclusive_scan<T>(v, sh, total) + (offs ? offs[blockIdx.x] : T(0));
   for (int i = 0; i < kScanItems; ++i) {
     if (base + i < cnt) data[base + i] = run;
     run += vals[i];
   }
 }
 
-// In-place exclusive scan of cnt int32 values (the total must fit int32).
-static fj_status exclusive_scan(int32_t* data, int64_t cnt, cudaStream_t st) {
+// In-place exclusive scan of cnt values (int32 totals must fit int32).
+template <typename T>
+static fj_status exclusive_scan(T* data, int64_t cnt, cudaStream_t st) {
   if (cnt <= 0) return FJ_OK;
   const int64_t blocks = (cnt + kScanChunk - 1) / kScanChunk;
   if (blocks == 1) {
-    k_scan_apply<<<1, kScanThreads, 0, st>>>(data, cnt, nullptr);
+    count_launches(1);
+    k_scan_apply<T><<<1, kScanThreads, 0, st>>>(data, cnt, nullptr);
     FJ_CUDA(cudaGetLastError());
     return FJ_OK;
   }
-  int32_t* sums = nullptr;
-  FJ_CUDA(cudaMallocAsync(&sums, blocks * sizeof(int32_t), st));
-  k_scan_reduce<<<(unsigned)blocks, kScanThreads, 0, st>>>(data, cnt, sums);
-  fj_status rc = exclusive_scan(sums, blocks, st);
+  T* sums = nullptr;
+  FJ_CUDA(cudaMallocAsync(&sums, blocks * sizeof(T), st));
+  count_launches(1);
+  k_scan_reduce<T><<<(unsigned)blocks, kScanThreads, 0, st>>>(data, cnt, sums);
+  fj_status rc = exclusive_scan<T>(sums, blocks, st);
   if (rc == FJ_OK) {
-    k_scan_apply<<<(unsigned)blocks, kScanThreads, 0, st>>>(data, cnt, sums);
+    count_launches(1);
+    k_scan_apply<T><<<(unsigned)blocks, kScanThreads, 0, st>>>(data, cnt, sums);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "k_scan_apply");
   }
@@ -273,15 +283,153 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_row_sums(WalkGraph g, doubl
   __shared__ TileSmem sm[kWalkWarps];
   const int warp = threadIdx.x >> 5;
   const int64_t wg = (int64_t)blockIdx.x * kWalkWarps + warp;
-  walk_tiles<double, 1, kRowSum>(g, nullptr, out, wc_row, wc_val, wg, &sm[warp]);
+  walk_tiles<double, 1, kRowSum>(g, nullptr, out, wc_row, wc_val, wg, (void*)&sm[warp]);
 }
 
 __global__ void k_dinv_weighted(WalkGraph g, const double* __restrict__ sums,
                                 const double* __restrict__ wc_val, float* __restrict__ dinv) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double d = row_total<double, 1>(i, sums[i], g.row_ptr, wc_val, g.tiles_per_warp, 0);
+    const double d = row_total<double, 1>(i, sums[i], g.row_ptr, wc_val, g.items_per_warp, 0);
     dinv[i] = (float)(1.0 / (1.0 + d));
+  }
+}
+
+// ------------------------------------------------------- solver order
+
+// Sort key of node i: decreasing degree (saturated), payload i.
+__global__ void k_degree_keys(const int32_t* __restrict__ row_ptr, int64_t n, int32_t* __restrict__ key,
+                              int32_t* __restrict__ id) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = row_ptr[i + 1] - row_ptr[i];
+    key[i] = kDegKeyMax - (d < kDegKeyMax ? d : kDegKeyMax);
+    id[i] = (int32_t)i;
+  }
+}
+
+// old2new[perm[i]] = i; deg_new[i] = degree of perm[i] (into rp_new[i]).
+__global__ void k_apply_perm(const int32_t* __restrict__ perm, const int32_t* __restrict__ row_ptr_old,
+                             int64_t n, int32_t* __restrict__ old2new, int32_t* __restrict__ rp_new) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i == n) {
+      rp_new[n] = 0;
+    } else {
+      const int32_t o = perm[i];
+      old2new[o] = (int32_t)i;
+      rp_new[i] = row_ptr_old[o + 1] - row_ptr_old[o];
+    }
+  }
+}
+
+// Entry p of the row-sorted input CSR moves to its place in the solver-order
+// CSR (same position inside its row), with the column renumbered.
+__global__ void k_copy_entries(const int32_t* __restrict__ key, const int32_t* __restrict__ col_old,
+                               const float* __restrict__ val_old, int64_t nnz,
+                               const int32_t* __restrict__ row_ptr_old, const int32_t* __restrict__ old2new,
+                               const int32_t* __restrict__ row_ptr_new, int32_t* __restrict__ col_new,
+                               float* __restrict__ val_new) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t ro = key[p];
+    const int32_t o = (int32_t)p - row_ptr_old[ro];
+    const int32_t pn = row_ptr_new[old2new[ro]] + o;
+    col_new[pn] = old2new[col_old[p]];
+    if (val_new) val_new[pn] = val_old[p];
+  }
+}
+
+// n_long = number of rows with more than kSellMaxLen entries (they come
+// first in solver order).
+__global__ void k_count_long(const int32_t* __restrict__ row_ptr, int64_t n, int64_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool lng = row_ptr[i + 1] - row_ptr[i] > kSellMaxLen;
+    const bool next = (i + 1 < n) && (row_ptr[i + 2] - row_ptr[i + 1] > kSellMaxLen);
+    if (lng && !next) out[0] = i + 1;
+  }
+}
+
+// slice_off[s] = 32 * (length of the slice's first, i.e. longest, row);
+// long_first[r] = number of chunks of long row r (both scanned afterwards).
+__global__ void k_layout_sizes(const int32_t* __restrict__ row_ptr, int64_t n, int64_t n_long,
+                               int64_t n_slices, int64_t* __restrict__ slice_off,
+                               int32_t* __restrict__ long_first) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n_slices + n_long;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n_slices) {
+      const int64_t r = n_long + 32 * i;
+      slice_off[i] = 32 * (int64_t)(row_ptr[r + 1] - row_ptr[r]);
+    } else if (i == n_slices) {
+      slice_off[n_slices] = 0;
+    } else {
+      const int64_t r = i - n_slices - 1;
+      long_first[r] = (r < n_long) ? (row_ptr[r + 1] - row_ptr[r] + kChunkLen - 1) / kChunkLen : 0;
+    }
+  }
+}
+
+// Fills the chunk table and the work-unit costs (chunks, then slices).
+__global__ void k_units(const int32_t* __restrict__ row_ptr, int64_t n_long, const int32_t* __restrict__ long_first,
+                        int64_t n_chunks, const int64_t* __restrict__ slice_off, int64_t n_slices,
+                        int32_t* __restrict__ chunk_row, int32_t* __restrict__ chunk_begin,
+                        int32_t* __restrict__ chunk_end, int64_t* __restrict__ unit_cost) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_long;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = row_ptr[r], e = row_ptr[r + 1];
+    for (int32_t c = long_first[r], q = 0; c < long_first[r + 1]; ++c, ++q) {
+      const int32_t cb = b + q * kChunkLen;
+      const int32_t ce = cb + kChunkLen < e ? cb + kChunkLen : e;
+      chunk_row[c] = (int32_t)r;
+      chunk_begin[c] = cb;
+      chunk_end[c] = ce;
+      unit_cost[c] = (ce - cb) + 16;
+    }
+  }
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s <= n_slices;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    unit_cost[n_chunks + s] = (s < n_slices) ? (slice_off[s + 1] - slice_off[s]) + 32 : 0;
+  }
+}
+
+// Sliced ELL padding: positions past a row's length get col = the row itself
+// (w (x_r - x_r) = 0 for any weight) and weight 0.  One warp per slice.
+__global__ void k_sell_pad(const int32_t* __restrict__ row_ptr, int64_t n, int64_t n_long, int64_t n_slices,
+                           const int64_t* __restrict__ slice_off, int32_t* __restrict__ sell_col,
+                           float* __restrict__ sell_val) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; s < n_slices;
+       s += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t row = n_long + 32 * s + lane;
+    const int32_t len = row < n ? row_ptr[row + 1] - row_ptr[row] : 0;
+    const int64_t off = slice_off[s];
+    const int32_t slen = (int32_t)((slice_off[s + 1] - off) >> 5);
+    for (int32_t p = len; p < slen; ++p) {
+      sell_col[off + 32 * (int64_t)p + lane] = row < n ? (int32_t)row : 0;
+      if (sell_val) sell_val[off + 32 * (int64_t)p + lane] = 0.0f;
+    }
+  }
+}
+
+// Sliced ELL entries of the short rows, from the solver-order CSR.  One
+// thread per entry; row lookup by the entry's row in the input CSR.
+__global__ void k_sell_fill(const int32_t* __restrict__ key, int64_t nnz, const int32_t* __restrict__ row_ptr_old,
+                            const int32_t* __restrict__ old2new, const int32_t* __restrict__ row_ptr_new,
+                            const int32_t* __restrict__ col_new, const float* __restrict__ val_new,
+                            int64_t n_long, const int64_t* __restrict__ slice_off, int32_t* __restrict__ sell_col,
+                            float* __restrict__ sell_val) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t ro = key[p];
+    const int32_t rn = old2new[ro];
+    if (rn < n_long) continue;
+    const int32_t o = (int32_t)p - row_ptr_old[ro];
+    const int32_t pn = row_ptr_new[rn] + o;
+    const int64_t sr = rn - n_long;
+    const int64_t pos = slice_off[sr >> 5] + 32 * (int64_t)o + (sr & 31);
+    sell_col[pos] = col_new[pn];
+    if (sell_val) sell_val[pos] = val_new[pn];
   }
 }
 
@@ -292,36 +440,115 @@ static unsigned grid_for(int64_t work, int threads) {
   return (unsigned)b;
 }
 
+// Stable LSD radix sort (8-bit digits) of N entries by key in [0, key_max].
+// FROM_EDGES: entries are generated from the edge list (first pass only).
+// Buffers kb/cb/vb[2] must hold N + kPad elements (vb may be null: no val);
+// returns the index (0/1) of the buffer set holding the result.
+static fj_status radix_sort(EntrySrc src, bool from_edges, int64_t N, int64_t key_max, int32_t* kb[2],
+                            int32_t* cb[2], float* vb[2], cudaStream_t st, int* result) {
+  int bits = 1;
+  while ((int64_t(1) << bits) <= key_max) ++bits;
+  const int passes = (bits + 7) / 8;
+  const int64_t nblocks = (N + kSortChunk - 1) / kSortChunk;
+  int cur = 0;
+  *result = 0;
+  if (N == 0) return FJ_OK;
+  int32_t* h = nullptr;
+  FJ_CUDA(cudaMallocAsync(&h, 256 * nblocks * sizeof(int32_t), st));
+  fj_status rc = FJ_OK;
+  for (int pass = 0; pass < passes && rc == FJ_OK; ++pass) {
+    const bool edges = from_edges && pass == 0;
+    EntrySrc s = src;
+    if (!edges) {
+      s.key = kb[cur];
+      s.col = cb[cur];
+      s.val = vb[cur];
+    }
+    const int dstb = edges ? 0 : 1 - cur;
+    count_launches(2);
+    if (edges) {
+      k_radix_hist<true><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, 0, h);
+    } else {
+      k_radix_hist<false><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, pass * 8, h);
+    }
+    rc = exclusive_scan<int32_t>(h, 256 * nblocks, st);
+    if (rc != FJ_OK) break;
+    if (edges) {
+      k_radix_scatter<true><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, 0, h, kb[dstb], cb[dstb], vb[dstb]);
+    } else {
+      k_radix_scatter<false><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, pass * 8, h, kb[dstb], cb[dstb],
+                                                                         vb[dstb]);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) rc = cuda_fail(e, "radix sort");
+    cur = dstb;
+  }
+  cudaFreeAsync(h, st);
+  *result = cur;
+  return rc;
+}
+
 }  // namespace fj
 
 using namespace fj;
 
 namespace {
 
-struct DevBuf {
-  void* p = nullptr;
-  cudaStream_t st = nullptr;
-  ~DevBuf() {
-    if (p) cudaFreeAsync(p, st);
+// Stream-ordered device allocations released at scope exit unless kept.
+struct Pool {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  bool failed = false;
+  explicit Pool(cudaStream_t s) : st(s) {}
+  template <typename T>
+  T* get(int64_t count) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, (size_t)std::max<int64_t>(count, 1) * sizeof(T), st) != cudaSuccess) {
+      cudaGetLastError();
+      failed = true;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+  void keep(const void* p) {
+    for (auto& q : ptrs)
+      if (q == p) q = nullptr;
+  }
+  ~Pool() {
+    for (void* p : ptrs)
+      if (p) cudaFreeAsync(p, st);
   }
 };
 
 }  // namespace
+
+void fj_free_graph_arrays(fj_graph* g, cudaStream_t st) {
+  void* arrays[] = {g->row_ptr,     g->col,       g->val,       g->dinv,      g->tile_row,
+                    g->perm,        g->long_first, g->chunk_row, g->chunk_begin, g->chunk_end,
+                    g->slice_off,   g->sell_col,  g->sell_val,  g->unit_prefix};
+  for (void* p : arrays)
+    if (p) cudaFreeAsync(p, st);
+}
 
 // Called by the C ABI (fj_api.cpp).  src/dst/w are device pointers.
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m,
                                 const int32_t* src, const int32_t* dst, const float* w,
                                 fj_graph** out) {
   const int64_t N = 2 * m;
-  // validation
-  DevBuf dflags;
-  dflags.st = st;
-  FJ_CUDA(cudaMallocAsync(&dflags.p, 16, st));
-  int* err = (int*)dflags.p;
-  unsigned long long* first_bad = (unsigned long long*)((char*)dflags.p + 8);
+  const bool weighted = (w != nullptr);
+  Pool pool(st);
+  // ---- validation
+  int* err = pool.get<int>(4);
+  if (!err) {
+    set_error("fj_graph_upload: out of device memory");
+    return FJ_ERR_OOM;
+  }
+  unsigned long long* first_bad = (unsigned long long*)(err + 2);
   FJ_CUDA(cudaMemsetAsync(err, 0, 4, st));
   FJ_CUDA(cudaMemsetAsync(first_bad, 0xff, 8, st));
   if (m > 0) {
+    count_launches(1);
     k_validate<<<grid_for(m, 256), 256, 0, st>>>(m, n, src, dst, w, err, first_bad);
     FJ_CUDA(cudaGetLastError());
   }
@@ -335,137 +562,183 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
               (herr & kErrBadId) ? "a node id outside [0, n)" : "a weight that is not finite and > 0");
     return FJ_ERR_GRAPH;
   }
+  auto oom = [&]() {
+    set_error("fj_graph_upload: out of device memory (n=%lld, m=%lld)", (long long)n, (long long)m);
+    return FJ_ERR_OOM;
+  };
 
-  const bool weighted = (w != nullptr);
-  // ping-pong entry buffers, padded so that tile staging never reads past
-  const int64_t cap = N + kPad;
-  DevBuf kb[2], cb[2], vb[2];
+  // ---- 1. input-order CSR by a stable sort of the directed entries by row
+  const int64_t cap = std::max<int64_t>(N, n) + kPad;
+  int32_t* kb[2];
+  int32_t* cb[2];
+  float* vb[2] = {nullptr, nullptr};
   for (int i = 0; i < 2; ++i) {
-    kb[i].st = cb[i].st = vb[i].st = st;
-    if (cudaMallocAsync(&kb[i].p, cap * 4, st) != cudaSuccess ||
-        cudaMallocAsync(&cb[i].p, cap * 4, st) != cudaSuccess ||
-        (weighted && cudaMallocAsync(&vb[i].p, cap * 4, st) != cudaSuccess)) {
-      cudaGetLastError();
-      set_error("fj_graph_upload: out of device memory for %lld entries", (long long)N);
-      return FJ_ERR_OOM;
-    }
+    kb[i] = pool.get<int32_t>(cap);
+    cb[i] = pool.get<int32_t>(cap);
+    if (weighted) vb[i] = pool.get<float>(cap);
   }
-  int bits = 1;
-  while ((int64_t(1) << bits) <= n) ++bits;  // keys are in [0, n]
-  const int passes = (bits + 7) / 8;
-  const int64_t nblocks = (N + kSortChunk - 1) / kSortChunk;
+  if (pool.failed) return oom();
+  EntrySrc es{src, dst, w, nullptr, nullptr, nullptr, (int32_t)n};
   int cur = 0;
-  if (N > 0) {
-    DevBuf hist;
-    hist.st = st;
-    FJ_CUDA(cudaMallocAsync(&hist.p, 256 * nblocks * sizeof(int32_t), st));
-    for (int pass = 0; pass < passes; ++pass) {
-      EntrySrc s{src, dst, w, (int32_t*)kb[cur].p, (int32_t*)cb[cur].p, (float*)vb[cur].p, (int32_t)n};
-      const int dstb = pass == 0 ? 0 : 1 - cur;
-      int32_t* h = (int32_t*)hist.p;
-      if (pass == 0) {
-        k_radix_hist<true><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, 0, h);
-      } else {
-        k_radix_hist<false><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, pass * 8, h);
-      }
-      FJ_CUDA(cudaGetLastError());
-      fj_status rc = exclusive_scan(h, 256 * nblocks, st);
-      if (rc != FJ_OK) return rc;
-      if (pass == 0) {
-        k_radix_scatter<true><<<(unsigned)nblocks, kSortThreads, 0, st>>>(
-            s, N, 0, h, (int32_t*)kb[dstb].p, (int32_t*)cb[dstb].p, (float*)vb[dstb].p);
-      } else {
-        k_radix_scatter<false><<<(unsigned)nblocks, kSortThreads, 0, st>>>(
-            s, N, pass * 8, h, (int32_t*)kb[dstb].p, (int32_t*)cb[dstb].p, (float*)vb[dstb].p);
-      }
-      FJ_CUDA(cudaGetLastError());
-      cur = dstb;
-    }
-  }
+  fj_status rc = radix_sort(es, true, N, n, kb, cb, vb, st, &cur);
+  if (rc != FJ_OK) return rc;
+  int32_t* key_old = kb[cur];
+  int32_t* col_old = cb[cur];
+  float* val_old = vb[cur];
+  int32_t* rp_old = pool.get<int32_t>(n + 1);
+  if (!rp_old) return oom();
+  count_launches(1);
+  k_row_ptr<<<grid_for(N + 1, 256), 256, 0, st>>>(key_old, N, n, rp_old);
+  FJ_CUDA(cudaGetLastError());
+
+  // ---- 2. solver order: stable sort of nodes by decreasing degree
+  int32_t* kb2[2] = {pool.get<int32_t>(n + kPad), pool.get<int32_t>(n + kPad)};
+  int32_t* cb2[2] = {pool.get<int32_t>(n + kPad), pool.get<int32_t>(n + kPad)};
+  float* vb2[2] = {nullptr, nullptr};
+  if (pool.failed) return oom();
+  count_launches(1);
+  k_degree_keys<<<grid_for(n, 256), 256, 0, st>>>(rp_old, n, kb2[0], cb2[0]);
+  FJ_CUDA(cudaGetLastError());
+  EntrySrc ns{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, (int32_t)n};
+  int cur2 = 0;
+  rc = radix_sort(ns, false, n, kDegKeyMax, kb2, cb2, vb2, st, &cur2);
+  if (rc != FJ_OK) return rc;
+  int32_t* perm = cb2[cur2];
 
   fj_graph* g = new fj_graph();
+  memset(g, 0, sizeof(*g));
   g->device = device;
   g->n = n;
   g->weighted = weighted ? 1 : 0;
-  auto fail = [&](fj_status rc) {
-    if (g->row_ptr) cudaFreeAsync(g->row_ptr, st);
-    if (g->dinv) cudaFreeAsync(g->dinv, st);
-    if (g->tile_row) cudaFreeAsync(g->tile_row, st);
+  auto fail = [&](fj_status code) {
+    fj_free_graph_arrays(g, st);
     delete g;
-    return rc;
+    return code;
   };
-  if (cudaMallocAsync(&g->row_ptr, (n + 1) * sizeof(int32_t), st) != cudaSuccess ||
-      cudaMallocAsync(&g->dinv, n * sizeof(float), st) != cudaSuccess) {
+  // perm is kept: the pool must not free it
+  g->perm = perm;
+  pool.keep(perm);
+  int32_t* old2new = pool.get<int32_t>(n);
+  g->row_ptr = (int32_t*)nullptr;
+  if (cudaMallocAsync(&g->row_ptr, (n + 1) * sizeof(int32_t), st) != cudaSuccess || !old2new) {
     cudaGetLastError();
-    set_error("fj_graph_upload: out of device memory");
-    return fail(FJ_ERR_OOM);
+    g->row_ptr = nullptr;
+    return fail(oom());
   }
-  k_row_ptr<<<grid_for(N + 1, 256), 256, 0, st>>>((int32_t*)kb[cur].p, N, n, g->row_ptr);
-  if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
+  count_launches(1);
+  k_apply_perm<<<grid_for(n + 1, 256), 256, 0, st>>>(perm, rp_old, n, old2new, g->row_ptr);
+  rc = exclusive_scan<int32_t>(g->row_ptr, n + 1, st);
+  if (rc != FJ_OK) return fail(rc);
+
+  // ---- 3. solver-order CSR
   int32_t nnz32 = 0;
   if (cudaMemcpyAsync(&nnz32, g->row_ptr + n, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return fail(FJ_ERR_CUDA);
-  g->nnz = nnz32;
-  // The sorted col/val buffers become the graph's (their tail past nnz holds
-  // self-loop entries or padding; zero the padding region after nnz).
-  g->col = (int32_t*)cb[cur].p;
-  cb[cur].p = nullptr;
-  if (cudaMemsetAsync(g->col + g->nnz, 0, kPad * 4, st) != cudaSuccess) return fail(FJ_ERR_CUDA);
-  if (weighted) {
-    g->val = (float*)vb[cur].p;
-    vb[cur].p = nullptr;
-    if (cudaMemsetAsync(g->val + g->nnz, 0, kPad * 4, st) != cudaSuccess) return fail(FJ_ERR_CUDA);
-  }
-  auto fail2 = [&](fj_status rc) {
-    if (g->col) cudaFreeAsync(g->col, st);
-    if (g->val) cudaFreeAsync(g->val, st);
-    return fail(rc);
-  };
-  // merge-path tile plan
-  g->n_tiles = (n + g->nnz + kTileItems - 1) / kTileItems;
-  if (cudaMallocAsync(&g->tile_row, (g->n_tiles + 1) * sizeof(int32_t), st) != cudaSuccess) {
+  const int64_t nnz = nnz32;
+  g->nnz = nnz;
+  if (cudaMallocAsync(&g->col, (nnz + kPad) * 4, st) != cudaSuccess ||
+      (weighted && cudaMallocAsync(&g->val, (nnz + kPad) * 4, st) != cudaSuccess)) {
     cudaGetLastError();
-    return fail2(FJ_ERR_OOM);
+    return fail(oom());
   }
-  k_tile_rows<<<grid_for(g->n_tiles + 1, 256), 256, 0, st>>>(g->row_ptr, n, g->nnz, g->n_tiles,
-                                                             g->tile_row);
-  if (cudaGetLastError() != cudaSuccess) return fail2(FJ_ERR_CUDA);
-  // Jacobi preconditioner 1 / (1 + d_i)
+  cudaMemsetAsync(g->col + nnz, 0, kPad * 4, st);
+  if (weighted) cudaMemsetAsync(g->val + nnz, 0, kPad * 4, st);
+  count_launches(1);
+  k_copy_entries<<<grid_for(nnz, 256), 256, 0, st>>>(key_old, col_old, val_old, nnz, rp_old, old2new,
+                                                     g->row_ptr, g->col, g->val);
+  if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
+
+  // ---- 4. long rows, slices, chunk table, work units
+  int64_t* scal = pool.get<int64_t>(2);
+  if (!scal) return fail(oom());
+  cudaMemsetAsync(scal, 0, 16, st);
+  count_launches(1);
+  k_count_long<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, scal);
+  int64_t n_long = 0;
+  if (cudaMemcpyAsync(&n_long, scal, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(FJ_ERR_CUDA);
+  g->n_long = n_long;
+  g->n_slices = (n - n_long + 31) / 32;
+  if (cudaMallocAsync(&g->slice_off, (g->n_slices + 1) * 8, st) != cudaSuccess ||
+      cudaMallocAsync(&g->long_first, (n_long + 1) * 4, st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(oom());
+  }
+  count_launches(1);
+  k_layout_sizes<<<grid_for(g->n_slices + n_long + 1, 256), 256, 0, st>>>(g->row_ptr, n, n_long, g->n_slices,
+                                                                        g->slice_off, g->long_first);
+  rc = exclusive_scan<int64_t>(g->slice_off, g->n_slices + 1, st);
+  if (rc == FJ_OK) rc = exclusive_scan<int32_t>(g->long_first, n_long + 1, st);
+  if (rc != FJ_OK) return fail(rc);
+  int64_t hs[2] = {0, 0};
+  int32_t hch = 0;
+  if (cudaMemcpyAsync(&hs[0], g->slice_off + g->n_slices, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&hch, g->long_first + n_long, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(FJ_ERR_CUDA);
+  g->sell_nnz = hs[0];
+  g->n_chunks = hch;
+  g->n_units = g->n_chunks + g->n_slices;
+  if (cudaMallocAsync(&g->sell_col, (g->sell_nnz + kPad) * 4, st) != cudaSuccess ||
+      (weighted && cudaMallocAsync(&g->sell_val, (g->sell_nnz + kPad) * 4, st) != cudaSuccess) ||
+      cudaMallocAsync(&g->chunk_row, std::max<int64_t>(g->n_chunks, 1) * 4, st) != cudaSuccess ||
+      cudaMallocAsync(&g->chunk_begin, std::max<int64_t>(g->n_chunks, 1) * 4, st) != cudaSuccess ||
+      cudaMallocAsync(&g->chunk_end, std::max<int64_t>(g->n_chunks, 1) * 4, st) != cudaSuccess ||
+      cudaMallocAsync(&g->unit_prefix, (g->n_units + 1) * 8, st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(oom());
+  }
+  count_launches(3);
+  k_units<<<grid_for(std::max(n_long, g->n_slices + 1), 256), 256, 0, st>>>(
+      g->row_ptr, n_long, g->long_first, g->n_chunks, g->slice_off, g->n_slices, g->chunk_row, g->chunk_begin,
+      g->chunk_end, g->unit_prefix);
+  k_sell_pad<<<grid_for(g->n_slices * 32, 256), 256, 0, st>>>(g->row_ptr, n, n_long, g->n_slices, g->slice_off,
+                                                              g->sell_col, g->sell_val);
+  k_sell_fill<<<grid_for(nnz, 256), 256, 0, st>>>(key_old, nnz, rp_old, old2new, g->row_ptr, g->col, g->val,
+                                                  n_long, g->slice_off, g->sell_col, g->sell_val);
+  if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
+  rc = exclusive_scan<int64_t>(g->unit_prefix, g->n_units + 1, st);
+  if (rc != FJ_OK) return fail(rc);
+
+  // ---- 5. merge-path tile plan and Jacobi preconditioner
+  g->n_tiles = (n + nnz + kTileItems - 1) / kTileItems;
+  if (cudaMallocAsync(&g->tile_row, (g->n_tiles + 1) * sizeof(int32_t), st) != cudaSuccess ||
+      cudaMallocAsync(&g->dinv, n * sizeof(float), st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(oom());
+  }
+  count_launches(1);
+  k_tile_rows<<<grid_for(g->n_tiles + 1, 256), 256, 0, st>>>(g->row_ptr, n, nnz, g->n_tiles, g->tile_row);
+  if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
   if (!weighted) {
+    count_launches(1);
     k_dinv_unit<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, g->dinv);
-    if (cudaGetLastError() != cudaSuccess) return fail2(FJ_ERR_CUDA);
+    if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
   } else {
     int64_t warps = g->n_tiles < 152 * 64 ? g->n_tiles : 152 * 64;
     if (warps < 1) warps = 1;
-    WalkGraph wg{g->row_ptr, g->col, g->val, g->tile_row, n, g->nnz, g->n_tiles,
-                 (g->n_tiles + warps - 1) / warps};
+    WalkGraph wg{g->row_ptr, g->col, g->val, g->tile_row, n, nnz, g->n_tiles, 1, {}};
+    set_tiles_per_warp(wg, (g->n_tiles + warps - 1) / warps);
     const int64_t blocks = (warps + kWalkWarps - 1) / kWalkWarps;
-    DevBuf sums, wrow, wval;
-    sums.st = wrow.st = wval.st = st;
-    if (cudaMallocAsync(&sums.p, n * 8, st) != cudaSuccess ||
-        cudaMallocAsync(&wrow.p, blocks * kWalkWarps * 4, st) != cudaSuccess ||
-        cudaMallocAsync(&wval.p, blocks * kWalkWarps * 8, st) != cudaSuccess) {
-      cudaGetLastError();
-      return fail2(FJ_ERR_OOM);
-    }
-    k_row_sums<<<(unsigned)blocks, kWalkWarps * 32, 0, st>>>(wg, (double*)sums.p, (int32_t*)wrow.p,
-                                                             (double*)wval.p);
-    k_dinv_weighted<<<grid_for(n, 256), 256, 0, st>>>(wg, (double*)sums.p, (double*)wval.p, g->dinv);
-    if (cudaGetLastError() != cudaSuccess) return fail2(FJ_ERR_CUDA);
+    double* sums = pool.get<double>(n);
+    int32_t* wrow = pool.get<int32_t>(blocks * kWalkWarps);
+    double* wval = pool.get<double>(blocks * kWalkWarps);
+    if (pool.failed) return fail(oom());
+    count_launches(2);
+    k_row_sums<<<(unsigned)blocks, kWalkWarps * 32, 0, st>>>(wg, sums, wrow, wval);
+    k_dinv_weighted<<<grid_for(n, 256), 256, 0, st>>>(wg, sums, wval, g->dinv);
+    if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
   }
-  if (cudaStreamSynchronize(st) != cudaSuccess) return fail2(FJ_ERR_CUDA);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(FJ_ERR_CUDA);
   *out = g;
   return FJ_OK;
 }
 
 fj_status fj_free_graph_device(fj_graph* g, cudaStream_t st) {
   if (!g) return FJ_OK;
-  cudaFreeAsync(g->row_ptr, st);
-  cudaFreeAsync(g->col, st);
-  if (g->val) cudaFreeAsync(g->val, st);
-  cudaFreeAsync(g->dinv, st);
-  cudaFreeAsync(g->tile_row, st);
+  fj_free_graph_arrays(g, st);
   FJ_CUDA(cudaStreamSynchronize(st));
   delete g;
   return FJ_OK;

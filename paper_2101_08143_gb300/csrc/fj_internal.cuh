@@ -1,11 +1,19 @@
 // fj_internal.cuh - shared device/host definitions of libfj (not installed).
 //
-// Data layout in device memory (one graph):
-//   row_ptr  int32[n+1]      CSR row starts of the off-diagonal part of L
-//   col      int32[nnz+pad]  neighbour ids, rows in input-edge order
-//   val      float[nnz+pad]  edge weights w_ij (absent for unit weights)
-//   dinv     float[n]        1 / (1 + d_i), the Jacobi preconditioner
-//   tile_row int32[NT+1]     merge-path row coordinate of every tile start
+// Data layout of one graph in device memory.  Nodes are renumbered in order
+// of decreasing degree ("solver order"; perm maps back to input ids), which
+// puts the hubs first and lets rows of similar length share a slice.
+//   row_ptr/col/val  CSR of the off-diagonal part of L in solver order,
+//                    each row's entries in input-edge order
+//   dinv             1 / (1 + d_i), the Jacobi preconditioner
+//   tile_row         merge-path row coordinate of every kTileItems tile
+//   rows [0, n_long) with more than kSellMaxLen entries ("long rows") are cut
+//                    into chunks of at most kChunkLen entries
+//   rows [n_long, n) are stored as sliced ELL: slices of 32 consecutive rows,
+//                    column-major inside a slice (entry p of the slice's lane
+//                    l at slice_off + 32 p + l), padded with col = own row
+//   unit_prefix      cumulative cost of the work units (chunks, then slices)
+//                    used to split every SpMV evenly over the warps
 // The diagonal 1 + d_i of I + L is never stored: (I + L) x is evaluated as
 // x_i + sum_j w_ij (x_i - x_j), the edge form of L = B^T W B (Sec. 2.1).
 #pragma once
@@ -13,15 +21,22 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/fj.h"
+#include "fj.h"
 
 namespace fj {
 
-// Merge-path items (row ends + nonzeros) per warp tile.
-constexpr int kTileItems = 256;
+// Merge-path items (row ends + nonzeros) per warp tile: 7 per lane, sized
+// so that two 16-warp blocks with float64 tile staging fit one SM.
+constexpr int kTileItems = 224;
 // Extra zeroed elements after col/val so that staging loads of the last tile
 // never leave the allocation.
 constexpr int kPad = 64;
+// Rows with at most kSellMaxLen entries go to sliced ELL; longer rows are
+// processed warp-wide in chunks of at most kChunkLen entries.
+constexpr int kSellMaxLen = 64;
+constexpr int kChunkLen = 2048;
+// Degree keys of the reordering sort saturate here (11-bit keys).
+constexpr int kDegKeyMax = 2047;
 
 // Error bits raised by device code.
 enum : int {
@@ -45,11 +60,29 @@ struct fj_graph {
   int64_t nnz;
   int64_t n_tiles;
   int weighted;
+  // CSR in solver order
   int32_t* row_ptr;
   int32_t* col;
   float* val;
   float* dinv;
   int32_t* tile_row;
+  int32_t* perm;  // perm[i] = input id of solver node i
+  // long rows [0, n_long) in chunks
+  int64_t n_long;
+  int64_t n_chunks;
+  int32_t* long_first;   // [n_long + 1] first chunk of each long row
+  int32_t* chunk_row;    // [n_chunks]
+  int32_t* chunk_begin;  // [n_chunks]
+  int32_t* chunk_end;    // [n_chunks]
+  // sliced ELL of rows [n_long, n)
+  int64_t n_slices;
+  int64_t sell_nnz;
+  int64_t* slice_off;  // [n_slices + 1]
+  int32_t* sell_col;
+  float* sell_val;  // absent for unit weights
+  // work units: chunks, then slices
+  int64_t n_units;
+  int64_t* unit_prefix;  // [n_units + 1]
 };
 
 namespace fj {
@@ -94,6 +127,8 @@ __device__ __forceinline__ int64_t merge_path_row(const int32_t* row_ptr,
 
 namespace fj {
 void set_error(const char* fmt, ...);
+// Counts kernel launches made by the library (all contexts, this process).
+void count_launches(int k);
 fj_status cuda_fail(cudaError_t e, const char* what);
 }  // namespace fj
 

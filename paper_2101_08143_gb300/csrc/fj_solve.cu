@@ -52,7 +52,12 @@ enum Mode { kModeMixed = 0, kModeFP64 = 1, kModeFP32 = 2 };
 
 template <typename VI>
 struct SolveParams {
-  WalkGraph g;
+  WalkGraph g;   // merge-path view (K >= 8)
+  SellGraph sg;  // sliced-ELL view (K <= 4)
+  const int32_t* perm;  // solver node -> input id
+  VI* hub_part;         // [n_chunks][K] chunk sums of multi-chunk rows
+  double* hub_part64;
+  int* hub_cnt;         // [n_long] finished chunks per long row
   const float* dinv;
   // problem (column c of this launch: s + c*ld)
   const double* s;
@@ -84,26 +89,25 @@ struct SolveParams {
   int mode;
 };
 
-// Grid-wide barrier with a bounded wait.  Returns false once any block has
-// given up (error bit kErrTimeout), after which every later barrier returns
-// at once so that all blocks leave the kernel.
-__device__ __forceinline__ bool grid_sync(Barrier* bar, int* status) {
+// Grid-wide barrier with a bounded wait.  The counter only grows: barrier
+// number e of a launch completes when it reaches e * gridDim.x.  Arrival is
+// one release-reduction per block (publishing the block's writes, ordered
+// before it by __syncthreads); the wait polls with acquire loads.  Returns
+// false once any block has given up (error bit kErrTimeout), after which every
+// later barrier returns at once so that all blocks leave the kernel.
+__device__ __forceinline__ bool grid_sync(Barrier* bar, int* status, unsigned& epoch) {
   __shared__ int ok_sh;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = (ld_volatile_i32(status) & kErrTimeout) == 0;
     if (gridDim.x > 1 && ok) {
-      const unsigned gen = ld_acquire_u32(&bar->gen);
-      __threadfence();
-      const unsigned arrived = atomicAdd(&bar->count, 1u);
-      if (arrived == gridDim.x - 1) {
-        atomicExch(&bar->count, 0u);
-        __threadfence();
-        atomicAdd(&bar->gen, 1u);
-      } else {
+      ++epoch;
+      const unsigned target = epoch * gridDim.x;
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+      if (ld_acquire_u32(&bar->count) < target) {
         const uint64_t t0 = global_ns();
         unsigned spins = 0;
-        while (ld_acquire_u32(&bar->gen) == gen) {
+        while (ld_acquire_u32(&bar->count) < target) {
           if ((++spins & 255u) == 0) {
             if ((ld_volatile_i32(status) & kErrTimeout) || global_ns() - t0 > kBarrierTimeoutNs) {
               atomicOr(status, kErrTimeout);
@@ -113,7 +117,6 @@ __device__ __forceinline__ bool grid_sync(Barrier* bar, int* status) {
           }
         }
       }
-      __threadfence();
     }
     ok_sh = ok;
   }
@@ -164,10 +167,30 @@ __device__ __forceinline__ void grid_reduce(const int (&slots)[NS], const double
 
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 
+// A lane holding partial sums for all K columns hands them to block_store,
+// which sums lanes of equal column lane % K: lane c < K gets the warp total of
+// column c, every other lane 0.
+template <typename T, int K>
+__device__ __forceinline__ double lane_share(T (&v)[K]) {
+  const int lane = threadIdx.x & 31;
+  double mine = 0.0;
+#pragma unroll
+  for (int cc = 0; cc < K; ++cc) {
+    double x = (double)v[cc];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(kFull, x, off);
+    if (lane == cc) mine = x;
+  }
+  return mine;
+}
+
 template <typename VI, int K>
-__global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams<VI> P) {
+__global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem* tsm = reinterpret_cast<TileSmem*>(smem_raw);
+  // per-warp tile staging, sized for the widest walk of this launch
+  constexpr size_t kTileBytes = tile_smem_bytes<VI, K>() > tile_smem_bytes<double, K>()
+                                    ? tile_smem_bytes<VI, K>()
+                                    : tile_smem_bytes<double, K>();
   __shared__ double red[7 * kWarps * K];
   __shared__ double res[NSLOT * K];
   __shared__ double alpha[K], beta[K], gam_prev[K], alpha_prev[K], rr_goal[K], mu[K], bb[K];
@@ -181,9 +204,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams<VI> P) {
   const int64_t gstride = (int64_t)gridDim.x * kThreads;
   const int c = threadIdx.x % K;
   const int64_t wg = (int64_t)blockIdx.x * kWarps + warp;
-  TileSmem* my_tsm = tsm + warp;
+  void* my_tsm = smem_raw + warp * kTileBytes;
   int* status = P.status;
   const bool fp32_mode = P.mode == kModeFP32;
+  unsigned epoch = 0;  // barriers passed (used by thread 0)
+  constexpr bool kSell = K <= 4;
+  // this warp's share of the sliced-ELL work units
+  int64_t u0 = 0, u1 = 0;
+  if (kSell) {
+    const int lane = threadIdx.x & 31;
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    int64_t v = 0;
+    if (lane < 2) v = sell_unit_start(P.sg, wg + lane, W);
+    u0 = __shfl_sync(kFull, v, 0);
+    u1 = __shfl_sync(kFull, v, 1);
+    for (int64_t i = gtid; i < P.sg.n_long; i += gstride) P.hub_cnt[i] = 0;
+  }
 
   // ---------------------------------------------------------------- setup
   {
@@ -193,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams<VI> P) {
     const int sl[1] = {S_SUM};
     block_store<K, 1>(v, sl, P.part, red);
   }
-  if (!grid_sync(P.bar, status)) return;
+  if (!grid_sync(P.bar, status, epoch)) return;
   {
     const int sl[1] = {S_SUM};
     grid_reduce<K, 1>(sl, P.part, res);
@@ -217,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams<VI> P) {
         const int64_t i = idx / K;
         double sb, qv, lq;
         if (init) {
-          sb = P.s[(int64_t)c * P.ld + i] - m;
+          sb = P.s[(int64_t)c * P.ld + P.perm[i]] - m;
           P.sbar[idx] = sb;
           P.q[idx] = 0.0;
           qv = 0.0;
@@ -226,7 +262,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams<VI> P) {
         } else {
           sb = P.sbar[idx];
           qv = P.q[idx];
-          lq = row_total<double, K>(i, P.t64[idx], P.g.row_ptr, P.wc_val64, P.g.tiles_per_warp, c);
+          if (kSell)
+            lq = P.t64[idx];
+          else
+            lq = row_total<double, K>(i, P.t64[idx], P.g.row_ptr, P.wc_val64, P.g.items_per_warp, c);
         }
         const double r64 = sb - qv - lq;
         a_rr64 += r64 * r64;
@@ -251,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams<VI> P) {
         block_store<K, 1>(vb, sb, P.part, red);
       }
     }
-    if (!grid_sync(P.bar, status)) return;
+    if (!grid_sync(P.bar, status, epoch)) return;
     {
       const int sl[7] = {S_RR64, S_P, S_C, S_CI, S_GAM, S_RR, S_UU};
       grid_reduce<K, 7>(sl, P.part, res);
@@ -321,12 +360,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams<VI> P) {
       // SpMV walk: t = off-diagonal part of (I + L) u, and the edge part of
       // (u, (I+L) u).
       {
-        const VI quad = walk_tiles<VI, K, kLap>(P.g, P.u, P.t, P.wc_row, P.wc_val, wg, my_tsm);
-        const double v[1] = {(double)quad};
+        double qv;
+        if constexpr (kSell) {
+          VI quad[K];
+#pragma unroll
+          for (int cc = 0; cc < K; ++cc) quad[cc] = VI(0);
+          sell_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.hub_cnt, u0, u1, quad);
+          qv = lane_share<VI, K>(quad);
+        } else {
+          qv = (double)walk_tiles<VI, K, kLap>(P.g, P.u, P.t, P.wc_row, P.wc_val, wg, my_tsm);
+        }
+        const double v[1] = {qv};
         const int sl[1] = {S_EQ};
         block_store<K, 1>(v, sl, P.part, red);
       }
-      if (!grid_sync(P.bar, status)) return;
+      if (!grid_sync(P.bar, status, epoch)) return;
       {
         const int sl[1] = {S_EQ};
         grid_reduce<K, 1>(sl, P.part, res);
@@ -368,23 +416,52 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams<VI> P) {
         const VI al = (VI)alpha[c], be = (VI)beta[c];
         const bool fst = first[c] != 0;
         VI l_gam = 0, l_rr = 0, l_uu = 0;
-        for (int64_t idx = gtid; idx < NK; idx += gstride) {
-          const int64_t i = idx / K;
-          const VI uv = P.u[idx];
-          const VI wv = uv + row_total<VI, K>(i, P.t[idx], P.g.row_ptr, P.wc_val, P.g.tiles_per_warp, c);
-          const VI pv = fst ? uv : uv + be * P.p[idx];
-          const VI dv = fst ? wv : wv + be * P.d[idx];
-          const VI xv = P.x[idx] + al * pv;
-          const VI rv = P.r[idx] - al * dv;
-          const VI un = P.dinv[i] * rv;
-          P.p[idx] = pv;
-          P.d[idx] = dv;
-          P.x[idx] = xv;
-          P.r[idx] = rv;
-          P.u[idx] = un;
-          l_gam += rv * un;
-          l_rr += rv * rv;
-          l_uu += un * un;
+        VI* __restrict__ vp = P.p;
+        VI* __restrict__ vd = P.d;
+        VI* __restrict__ vx = P.x;
+        VI* __restrict__ vr = P.r;
+        VI* __restrict__ vu = P.u;
+        const VI* __restrict__ vt = P.t;
+        const float* __restrict__ vdinv = P.dinv;
+        // kV elements per thread per round, all loads issued before use
+        constexpr int kV = 2;
+        for (int64_t base = gtid; base < NK; base += kV * gstride) {
+          VI uv[kV], tv[kV], pv[kV], dv[kV], xv[kV], rv[kV], di[kV];
+#pragma unroll
+          for (int e = 0; e < kV; ++e) {
+            const int64_t idx = base + e * gstride;
+            if (idx < NK) {
+              const int64_t i = idx / K;
+              uv[e] = vu[idx];
+              tv[e] = kSell ? vt[idx]
+                            : row_total<VI, K>(i, vt[idx], P.g.row_ptr, P.wc_val, P.g.items_per_warp, c);
+              pv[e] = fst ? VI(0) : vp[idx];
+              dv[e] = fst ? VI(0) : vd[idx];
+              xv[e] = vx[idx];
+              rv[e] = vr[idx];
+              di[e] = vdinv[i];
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < kV; ++e) {
+            const int64_t idx = base + e * gstride;
+            if (idx < NK) {
+              const VI wv = uv[e] + tv[e];
+              const VI pn = uv[e] + be * pv[e];
+              const VI dn = wv + be * dv[e];
+              const VI xn = xv[e] + al * pn;
+              const VI rn = rv[e] - al * dn;
+              const VI un = di[e] * rn;
+              vp[idx] = pn;
+              vd[idx] = dn;
+              vx[idx] = xn;
+              vr[idx] = rn;
+              vu[idx] = un;
+              l_gam += rn * un;
+              l_rr += rn * rn;
+              l_uu += un * un;
+            }
+          }
         }
         a_gam = (double)l_gam;
         a_rr = (double)l_rr;
@@ -393,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams<VI> P) {
         const int sl[3] = {S_GAM, S_RR, S_UU};
         block_store<K, 3>(v, sl, P.part, red);
       }
-      if (!grid_sync(P.bar, status)) return;
+      if (!grid_sync(P.bar, status, epoch)) return;
       {
         const int sl[3] = {S_GAM, S_RR, S_UU};
         grid_reduce<K, 3>(sl, P.part, res);
@@ -424,20 +501,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams<VI> P) {
 
     // q += x (float64), then the residual walk t64 = L q and sum w (q_i-q_j)^2
     for (int64_t idx = gtid; idx < NK; idx += gstride) P.q[idx] += (double)P.x[idx];
-    if (!grid_sync(P.bar, status)) return;
+    if (!grid_sync(P.bar, status, epoch)) return;
     {
-      const double quad = walk_tiles<double, K, kLap>(P.g, P.q, P.t64, P.wc_row, P.wc_val64, wg, my_tsm);
+      double quad;
+      if constexpr (kSell) {
+        double qd[K];
+#pragma unroll
+        for (int cc = 0; cc < K; ++cc) qd[cc] = 0.0;
+        sell_walk<double, K>(P.sg, P.q, P.t64, P.hub_part64, P.hub_cnt, u0, u1, qd);
+        quad = lane_share<double, K>(qd);
+      } else {
+        quad = walk_tiles<double, K, kLap>(P.g, P.q, P.t64, P.wc_row, P.wc_val64, wg, my_tsm);
+      }
       const double v[1] = {quad};
       const int sl[1] = {S_D};
       block_store<K, 1>(v, sl, P.part, red);
     }
-    if (!grid_sync(P.bar, status)) return;
+    if (!grid_sync(P.bar, status, epoch)) return;
   }
 
   // ---------------------------------------------------------------- output
   if (P.z_out) {
     for (int64_t idx = gtid; idx < NK; idx += gstride)
-      P.z_out[(int64_t)c * P.ld + idx / K] = P.q[idx] + mu[c];
+      P.z_out[(int64_t)c * P.ld + P.perm[idx / K]] = P.q[idx] + mu[c];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     int all_done = 1;
@@ -460,7 +546,7 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
                             int64_t ld, double* z, double* quant, double* resid, int* status,
                             char* ws, size_t ws_bytes, const fj_opts& o, int mode, int max_blocks) {
   auto kern = k_solve<VI, K>;
-  const size_t dyn = kWarps * sizeof(TileSmem);
+  const size_t dyn = (K <= 4) ? 0 : kWarps * std::max(tile_smem_bytes<VI, K>(), tile_smem_bytes<double, K>());
   FJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int per_sm = 0;
   FJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, dyn));
@@ -470,8 +556,9 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   }
   const int64_t n = g->n;
   // grid: enough blocks for the work, at most what is co-resident
+  // about 16 path items per thread before the grid stops growing
   const int64_t work = n * K + g->nnz * K;
-  int64_t want = (work + 8 * kThreads * 64 - 1) / (8 * kThreads * 64);
+  int64_t want = (work + kThreads * 16 - 1) / (kThreads * 16);
   if (want < 1) want = 1;
   int64_t cap = (int64_t)std::min(per_sm, kMaxBlocksPerSM) * num_sms;
   if (max_blocks > 0 && cap > max_blocks) cap = max_blocks;
@@ -488,7 +575,13 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
     return (void*)p;
   };
   SolveParams<VI> P;
-  P.g = WalkGraph{g->row_ptr, g->col, g->val, g->tile_row, n, g->nnz, g->n_tiles, tpw};
+  P.g = WalkGraph{g->row_ptr, g->col, g->val, g->tile_row, n, g->nnz, g->n_tiles, tpw, {}};
+  set_tiles_per_warp(P.g, tpw);
+  P.sg = SellGraph{g->row_ptr,   g->col,       g->val,      g->long_first, g->chunk_row,
+                   g->chunk_begin, g->chunk_end, g->slice_off, g->sell_col,   g->sell_val,
+                   g->unit_prefix, n,            g->n_long,   g->n_chunks,   g->n_slices,
+                   g->n_units};
+  P.perm = g->perm;
   P.dinv = g->dinv;
   P.s = s;
   P.ld = ld;
@@ -509,6 +602,9 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.wc_val = (VI*)take(warps * K * sizeof(VI));
   P.wc_val64 = (double*)take(warps * K * 8);
   P.part = (double*)take((size_t)blocks * NSLOT * K * 8);
+  P.hub_part = (VI*)take(std::max<int64_t>(g->n_chunks, 1) * K * sizeof(VI));
+  P.hub_part64 = (double*)take(std::max<int64_t>(g->n_chunks, 1) * K * 8);
+  P.hub_cnt = (int*)take(std::max<int64_t>(g->n_long, 1) * 4);
   P.bar = (Barrier*)take(sizeof(Barrier));
   if (off > ws_bytes) {
     set_error("internal: workspace too small (%zu > %zu)", off, ws_bytes);
@@ -522,6 +618,7 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   FJ_CUDA(cudaMemsetAsync(P.bar, 0, sizeof(Barrier), st));
   void* args[] = {&P};
   FJ_CUDA(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(kThreads), args, dyn, st));
+  count_launches(1);
   return FJ_OK;
 }
 
@@ -544,6 +641,9 @@ size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int n
   add(warps * K * inner_bytes);
   add(warps * K * 8);
   add((size_t)blocks * NSLOT * K * 8);
+  add(std::max<int64_t>(g->n_chunks, 1) * K * inner_bytes);
+  add(std::max<int64_t>(g->n_chunks, 1) * K * 8);
+  add(std::max<int64_t>(g->n_long, 1) * 4);
   add(sizeof(Barrier));
   return b;
 }

@@ -32,6 +32,48 @@ struct TileSmem {
   float val[kTileItems];
 };
 
+// Narrow right-hand sides (K * sizeof(T) <= 8) also stage the gathered
+// neighbour values x_j and the row values x_r of the tile, so that all of a
+// tile's gathers are in flight at once and the walk itself touches only
+// shared memory.
+template <typename T, int K>
+struct StagesX {
+  static constexpr bool value = K * sizeof(T) <= 8;
+};
+
+template <typename T, int K>
+struct TileSmemX {
+  int32_t re[kTileItems + 1];  // row_ptr[r0+1 .. r1+1]
+  float val[kTileItems];
+  T xj[kTileItems * K];        // x[col[k0 + j]]
+  T xr[(kTileItems + 1) * K];  // x[r0 + j]
+};
+
+template <typename T, int K>
+__host__ __device__ constexpr size_t tile_smem_bytes() {
+  return StagesX<T, K>::value ? sizeof(TileSmemX<T, K>) : sizeof(TileSmem);
+}
+
+// Unsigned 32-bit division by a run-time invariant d >= 1 with one multiply
+// (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, Sec. 4): q = (t + ((a - t) >> 1)) >> (l - 1),
+// t = umulhi(m, a), l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1.
+struct FastDiv {
+  uint32_t d, m, s;  // s = l - 1 (d >= 2); d == 1 is handled apart
+  __host__ void init(uint32_t div) {
+    d = div;
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < div) ++l;
+    m = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - div)) / div + 1);
+    s = l ? l - 1 : 0;
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t a) const {
+    if (d == 1) return a;
+    const uint32_t t = __umulhi(m, a);
+    return (t + ((a - t) >> 1)) >> s;
+  }
+};
+
 struct WalkGraph {
   const int32_t* row_ptr;
   const int32_t* col;
@@ -41,7 +83,13 @@ struct WalkGraph {
   int64_t nnz;
   int64_t n_tiles;
   int64_t tiles_per_warp;
+  FastDiv items_per_warp;  // kTileItems * tiles_per_warp (n + nnz < 2^32)
 };
+
+inline void set_tiles_per_warp(WalkGraph& g, int64_t tpw) {
+  g.tiles_per_warp = tpw;
+  g.items_per_warp.init((uint32_t)(tpw * kTileItems));
+}
 
 enum WalkMode { kRowSum = 0, kLap = 1 };
 
@@ -54,7 +102,12 @@ enum WalkMode { kRowSum = 0, kLap = 1 };
 template <typename T, int K, int MODE>
 __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict__ x,
                                         T* __restrict__ out, int32_t* __restrict__ wc_row,
-                                        T* __restrict__ wc_val, int64_t wg, TileSmem* sm) {
+                                        T* __restrict__ wc_val, int64_t wg, void* smem) {
+  constexpr bool kStageX = (MODE == kLap) && StagesX<T, K>::value;
+  TileSmem* sm = reinterpret_cast<TileSmem*>(smem);
+  TileSmemX<T, K>* smx = reinterpret_cast<TileSmemX<T, K>*>(smem);
+  int32_t* s_re = kStageX ? smx->re : sm->re;
+  float* s_val = kStageX ? smx->val : sm->val;
   constexpr int G = 32 / K;           // walkers per warp
   constexpr int IPW = kTileItems / G;  // items per walker per tile
   const int lane = threadIdx.x & 31;
@@ -67,24 +120,91 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
   T quad = T(0);
   if (t_begin >= t_end) return quad;
 
-  int32_t carry_row = g.tile_row[t_begin];
+  // tile row coordinates of 32 tiles at a time live in one register per lane
+  int32_t trow = g.tile_row[t_begin + (lane < t_end - t_begin + 1 ? lane : 0)];
+  int64_t tbase = t_begin;
+  int32_t carry_row = __shfl_sync(kFull, trow, 0);
   T carry = T(0);
   for (int64_t t = t_begin; t < t_end; ++t) {
+    if (t + 1 - tbase >= 32) {  // refill the coordinate window
+      tbase = t;
+      const int64_t q = t + lane;
+      trow = g.tile_row[q <= t_end ? q : t_end];
+    }
+    const int32_t r0 = __shfl_sync(kFull, trow, (int)(t - tbase));
+    const int32_t r1 = __shfl_sync(kFull, trow, (int)(t + 1 - tbase));
     const int64_t d0 = t * kTileItems;
     int64_t d1 = d0 + kTileItems;
     if (d1 > total) d1 = total;
-    const int64_t r0 = g.tile_row[t];
-    const int64_t r1 = g.tile_row[t + 1];
     const int32_t k0 = (int32_t)(d0 - r0);
     const int32_t k1 = (int32_t)(d1 - r1);
-    const int64_t rlast = (r1 < g.n - 1) ? r1 : (g.n - 1);
-    const int nre = (int)(rlast - r0 + 1);
+    const int32_t rlast = (r1 < g.n - 1) ? r1 : (int32_t)(g.n - 1);
+    const int nre = rlast - r0 + 1;
     const int nk = k1 - k0;
     __syncwarp();
-    for (int j = lane; j < nre; j += 32) sm->re[j] = g.row_ptr[r0 + 1 + j];
-    for (int j = lane; j < nk; j += 32) {
-      sm->col[j] = g.col[k0 + j];
-      if (g.val) sm->val[j] = g.val[k0 + j];
+    // Staging in two waves, each issuing all of its global loads before any
+    // shared-memory store (a store between loads would serialise them):
+    // wave 1 row ends, columns and weights; wave 2 the gathers x[col], x[r].
+    constexpr int kPer = (kTileItems + 31) / 32;
+    int32_t cj[kPer];
+    {
+      int32_t rev[kPer + 1];
+      float wv[kPer];
+#pragma unroll
+      for (int u = 0; u <= kPer; ++u) {
+        const int j = lane + 32 * u;
+        rev[u] = (j < nre) ? g.row_ptr[r0 + 1 + j] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int j = lane + 32 * u;
+        cj[u] = (j < nk) ? g.col[k0 + j] : 0;
+        wv[u] = (g.val && j < nk) ? g.val[k0 + j] : 1.0f;
+      }
+#pragma unroll
+      for (int u = 0; u <= kPer; ++u) {
+        const int j = lane + 32 * u;
+        if (j < nre) s_re[j] = rev[u];
+      }
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int j = lane + 32 * u;
+        if (j < nk) {
+          s_val[j] = wv[u];
+          if (!kStageX) sm->col[j] = cj[u];
+        }
+      }
+    }
+    if (kStageX) {
+      T xg[kPer][K];
+      T xrv[kPer + 1];
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int j = lane + 32 * u;
+#pragma unroll
+        for (int cc = 0; cc < K; ++cc) xg[u][cc] = (j < nk) ? x[(int64_t)cj[u] * K + cc] : T(0);
+      }
+      // x of the tile's rows: nre * K consecutive values
+#pragma unroll
+      for (int u = 0; u <= kPer; ++u) {
+        const int e = lane + 32 * u;
+        xrv[u] = (e < nre * K) ? x[(int64_t)r0 * K + e] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int j = lane + 32 * u;
+        if (j < nk) {
+#pragma unroll
+          for (int cc = 0; cc < K; ++cc) smx->xj[j * K + cc] = xg[u][cc];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u <= kPer; ++u) {
+        const int e = lane + 32 * u;
+        if (e < nre * K) smx->xr[e] = xrv[u];
+      }
+      // rows beyond 32 * (kPer + 1) / K of a tile (only when K > 1)
+      for (int e = lane + 32 * (kPer + 1); e < nre * K; e += 32) smx->xr[e] = x[(int64_t)r0 * K + e];
     }
     __syncwarp();
 
@@ -96,32 +216,33 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
     // merge-path split of local diagonal dl inside the tile
     int lo = dl - nk;
     if (lo < 0) lo = 0;
-    int hi = (int)(r1 - r0);
+    int hi = r1 - r0;
     if (hi > dl) hi = dl;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if ((sm->re[mid - 1] - k0) + mid <= dl)
+      if ((s_re[mid - 1] - k0) + mid <= dl)
         lo = mid;
       else
         hi = mid - 1;
     }
-    int64_t r = r0 + lo;
-    int k = dl - lo;  // local nonzero index
+    int rl = lo;       // local row
+    int k = dl - lo;   // local nonzero index
     T xr = T(0);
-    if (MODE == kLap && r < g.n) xr = x[r * K + c];
+    if (MODE == kLap && r0 + rl < g.n)
+      xr = kStageX ? smx->xr[rl * K + c] : x[(int64_t)(r0 + rl) * K + c];
     T acc = T(0);
     bool femit = false;
     T fval = T(0);
-    const int64_t frow = r;
+    const int frl = rl;
     for (int it = dl; it < de; ++it) {
-      const int rend = sm->re[r - r0] - k0;
+      const int rend = s_re[rl] - k0;
       if (k < rend) {
-        const float w = g.val ? sm->val[k] : 1.0f;
+        const float w = g.val ? s_val[k] : 1.0f;
         if (MODE == kRowSum) {
           acc += T(w);
         } else {
-          const int32_t j = sm->col[k];
-          const T df = xr - x[(int64_t)j * K + c];
+          const T xj = kStageX ? smx->xj[k * K + c] : x[(int64_t)sm->col[k] * K + c];
+          const T df = xr - xj;
           const T tw = T(w) * df;
           acc += tw;
           quad += tw * df;
@@ -132,14 +253,15 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
           femit = true;
           fval = acc;
         } else {
-          out[r * K + c] = acc;
+          out[(int64_t)(r0 + rl) * K + c] = acc;
         }
         acc = T(0);
-        ++r;
-        if (MODE == kLap && r < g.n) xr = x[r * K + c];
+        ++rl;
+        if (MODE == kLap && r0 + rl < g.n)
+          xr = kStageX ? smx->xr[rl * K + c] : x[(int64_t)(r0 + rl) * K + c];
       }
     }
-    int32_t crow = (int32_t)r;
+    int32_t crow = r0 + rl;
     T cval = acc;
     if (gw == 0) {
       if (femit)
@@ -155,7 +277,7 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
       if (gw >= off && kr == crow) scan += v;
     }
     const T prev = __shfl_up_sync(kFull, scan, K);
-    if (femit) out[frow * K + c] = fval + (gw > 0 ? prev : T(0));
+    if (femit) out[(int64_t)(r0 + frl) * K + c] = fval + (gw > 0 ? prev : T(0));
     carry = __shfl_sync(kFull, scan, (G - 1) * K + c);
     carry_row = __shfl_sync(kFull, crow, (G - 1) * K + c);
   }
@@ -164,17 +286,208 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
   return quad;
 }
 
+// ------------------------------------------------------------ sliced ELL
+//
+// Narrow right-hand sides (K <= 4) use the sliced-ELL layout: each lane owns
+// one row of a 32-row slice and walks it entry by entry, so every load of
+// col/val is one coalesced 128-byte line, the K values of x_j come in one
+// vector load, and a row's sum is accumulated by one lane in entry order.
+// Long rows are cut into chunks processed by a whole warp (lanes stride over
+// the chunk, then a fixed xor-tree reduction).  A row with several chunks is
+// finished by the warp that completes its last chunk: chunk sums go to
+// part[], a per-row counter counts finished chunks, and the last finisher
+// adds the row's chunk sums in chunk order.  Every row sum is therefore the
+// same bits whichever warp computes which unit.
+
+struct SellGraph {
+  const int32_t* row_ptr;  // solver-order CSR (long rows)
+  const int32_t* col;
+  const float* val;
+  const int32_t* long_first;
+  const int32_t* chunk_row;
+  const int32_t* chunk_begin;
+  const int32_t* chunk_end;
+  const int64_t* slice_off;
+  const int32_t* sell_col;
+  const float* sell_val;
+  const int64_t* unit_prefix;
+  int64_t n;
+  int64_t n_long;
+  int64_t n_chunks;
+  int64_t n_slices;
+  int64_t n_units;
+};
+
+template <typename T, int K>
+__device__ __forceinline__ void load_k(const T* __restrict__ p, T (&v)[K]) {
+  if constexpr (K * sizeof(T) == 16 && sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else if constexpr (K * sizeof(T) == 16 && sizeof(T) == 8) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  } else if constexpr (K * sizeof(T) == 8 && sizeof(T) == 4) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  } else {
+#pragma unroll
+    for (int cc = 0; cc < K; ++cc) v[cc] = p[cc];
+  }
+}
+
+// First work unit of warp w of W when units are split by cumulative cost.
+__device__ __forceinline__ int64_t sell_unit_start(const SellGraph& g, int64_t w, int64_t W) {
+  const int64_t total = g.unit_prefix[g.n_units];
+  const int64_t target = (w * total + W - 1) / W;  // ceil(w * total / W)
+  int64_t lo = 0, hi = g.n_units;  // first u with prefix[u] >= target
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (g.unit_prefix[mid] < target)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// out[r*K+c] = sum_j w_rj (x[r*K+c] - x[j*K+c]) for every row of units
+// [u0, u1); quad[c] accumulates this lane's share of sum w (x_r - x_j)^2.
+template <typename T, int K>
+__device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
+                                          T* __restrict__ part, int* __restrict__ cnt, int64_t u0,
+                                          int64_t u1, T (&quad)[K]) {
+  const int lane = threadIdx.x & 31;
+  // entries in flight per lane between two dependent round trips
+  constexpr int kB = (K * sizeof(T) <= 4) ? 8 : 4;
+  for (int64_t u = u0; u < u1; ++u) {
+    if (u < g.n_chunks) {
+      const int32_t r = g.chunk_row[u];
+      const int32_t b = g.chunk_begin[u], e = g.chunk_end[u];
+      T xr[K], acc[K];
+      load_k<T, K>(x + (int64_t)r * K, xr);
+#pragma unroll
+      for (int cc = 0; cc < K; ++cc) acc[cc] = T(0);
+      // batches of kB entries per lane: all index loads, then all gathers
+      for (int32_t p0 = b; p0 < e; p0 += 32 * kB) {
+        int32_t j[kB];
+        float w[kB];
+#pragma unroll
+        for (int q = 0; q < kB; ++q) {
+          const int32_t p = p0 + 32 * q + lane;
+          j[q] = p < e ? g.col[p] : r;
+          w[q] = (p < e && g.val) ? g.val[p] : (p < e ? 1.0f : 0.0f);
+        }
+        T xj[kB][K];
+#pragma unroll
+        for (int q = 0; q < kB; ++q) load_k<T, K>(x + (int64_t)j[q] * K, xj[q]);
+#pragma unroll
+        for (int q = 0; q < kB; ++q) {
+#pragma unroll
+          for (int cc = 0; cc < K; ++cc) {
+            const T df = xr[cc] - xj[q][cc];
+            const T tw = T(w[q]) * df;
+            acc[cc] += tw;
+            quad[cc] += tw * df;
+          }
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < K; ++cc) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[cc] += __shfl_xor_sync(kFull, acc[cc], off);
+      }
+      T mine = acc[0];
+#pragma unroll
+      for (int cc = 1; cc < K; ++cc)
+        if (lane == cc) mine = acc[cc];
+      const int32_t f = g.long_first[r];
+      const int32_t nch = g.long_first[r + 1] - f;
+      if (nch == 1) {
+        if (lane < K) out[(int64_t)r * K + lane] = mine;
+      } else {
+        if (lane < K) {
+          part[u * K + lane] = mine;
+          __threadfence();
+        }
+        __syncwarp();
+        int done = 0;
+        if (lane == 0) done = atomicAdd(&cnt[r], 1) == nch - 1;
+        done = __shfl_sync(kFull, done, 0);
+        if (done) {
+          __threadfence();
+          T tot[K];
+#pragma unroll
+          for (int cc = 0; cc < K; ++cc) tot[cc] = T(0);
+          for (int32_t q = f + lane; q < f + nch; q += 32) {
+#pragma unroll
+            for (int cc = 0; cc < K; ++cc) tot[cc] += __ldcg(&part[(int64_t)q * K + cc]);
+          }
+#pragma unroll
+          for (int cc = 0; cc < K; ++cc) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) tot[cc] += __shfl_xor_sync(kFull, tot[cc], off);
+          }
+          T t = tot[0];
+#pragma unroll
+          for (int cc = 1; cc < K; ++cc)
+            if (lane == cc) t = tot[cc];
+          if (lane < K) out[(int64_t)r * K + lane] = t;
+          if (lane == 0) cnt[r] = 0;
+        }
+      }
+    } else {
+      const int64_t s = u - g.n_chunks;
+      const int64_t off = g.slice_off[s];
+      const int32_t len = (int32_t)((g.slice_off[s + 1] - off) >> 5);
+      const int64_t row = g.n_long + 32 * s + lane;
+      if (row < g.n) {
+        T xr[K], acc[K];
+        load_k<T, K>(x + row * K, xr);
+#pragma unroll
+        for (int cc = 0; cc < K; ++cc) acc[cc] = T(0);
+        const int32_t* __restrict__ cp = g.sell_col + off + lane;
+        const float* __restrict__ vp = g.sell_val ? g.sell_val + off + lane : nullptr;
+        // batches of kB entries: all index loads, then all gathers
+        for (int32_t p0 = 0; p0 < len; p0 += kB) {
+          int32_t j[kB];
+          float w[kB];
+#pragma unroll
+          for (int q = 0; q < kB; ++q) {
+            const bool in = p0 + q < len;
+            j[q] = in ? cp[32 * (p0 + q)] : (int32_t)row;
+            w[q] = in ? (vp ? vp[32 * (p0 + q)] : 1.0f) : 0.0f;
+          }
+          T xj[kB][K];
+#pragma unroll
+          for (int q = 0; q < kB; ++q) load_k<T, K>(x + (int64_t)j[q] * K, xj[q]);
+#pragma unroll
+          for (int q = 0; q < kB; ++q) {
+#pragma unroll
+            for (int cc = 0; cc < K; ++cc) {
+              const T df = xr[cc] - xj[q][cc];
+              const T tw = T(w[q]) * df;
+              acc[cc] += tw;
+              quad[cc] += tw * df;
+            }
+          }
+        }
+#pragma unroll
+        for (int cc = 0; cc < K; ++cc) out[row * K + cc] = acc[cc];
+      }
+    }
+  }
+}
+
 // Adds to `own` (the value written for row i by the warp holding its row
 // end) the carries of the warps whose runs end inside row i, in warp order.
 template <typename T, int K>
 __device__ __forceinline__ T row_total(int64_t i, T own, const int32_t* __restrict__ row_ptr,
-                                       const T* __restrict__ wc_val, int64_t tiles_per_warp,
-                                       int c) {
-  const int64_t a = i + row_ptr[i];
-  const int64_t b = i + row_ptr[i + 1];
-  const int64_t wa = (a / kTileItems) / tiles_per_warp;
-  const int64_t wb = (b / kTileItems) / tiles_per_warp;
-  for (int64_t w = wa; w < wb; ++w) own += wc_val[w * K + c];
+                                       const T* __restrict__ wc_val, const FastDiv& ipw, int c) {
+  const uint32_t a = (uint32_t)i + (uint32_t)row_ptr[i];
+  const uint32_t b = (uint32_t)i + (uint32_t)row_ptr[i + 1];
+  const uint32_t wa = ipw.div(a);
+  const uint32_t wb = ipw.div(b);
+  for (uint32_t w = wa; w < wb; ++w) own += wc_val[(int64_t)w * K + c];
   return own;
 }
 

@@ -66,6 +66,7 @@ _SIGNATURES = {
     "fj_default_opts": (None, [ctypes.POINTER(Opts)]),
     "fj_last_error": (ctypes.c_char_p, []),
     "fj_version": (ctypes.c_char_p, []),
+    "fj_kernel_launches": (ctypes.c_int64, []),
     "fj_create": (ctypes.c_int32, [ctypes.c_int, ctypes.POINTER(_P)]),
     "fj_destroy": (ctypes.c_int32, [_P]),
     "fj_set_stream": (ctypes.c_int32, [_P, _P]),
@@ -243,7 +244,14 @@ class Context:
             s2 = s.reshape(n, -1)
             k = s2.shape[1]
             sf = np.asfortranarray(s2)
-            z = np.empty((n, k), dtype=np.float64, order="F") if want_z else None
+            z = None
+            if want_z:
+                if z_out is not None:
+                    z = z_out
+                    if z.dtype != np.float64 or not z.flags.f_contiguous or z.size != n * k:
+                        raise ValueError("host z_out must be F-contiguous float64 with n*k elements")
+                else:
+                    z = np.empty((n, k), dtype=np.float64, order="F")
             sp = sf.ctypes.data
             zp = z.ctypes.data if z is not None else None
             o.flags = FJ_HOST_PTRS
