@@ -189,6 +189,34 @@ fj_status fj_quantities(fj_ctx* ctx, const fj_graph* g, int32_t k,
                         const double* s, fj_quant* out, const fj_opts* opts,
                         fj_info* info);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free solve.  The paper has no counterpart: this entry point
+ * serves callers that must not allocate device memory while solving - code
+ * inside a latency-critical loop, where cudaMalloc/cudaFree could stall the
+ * whole device, and programs whose device memory belongs to another
+ * allocator.  It runs the same solver as fj_solve_ex but takes every scratch
+ * buffer from one array of FJ_FIXED_SCRATCH_BYTES bytes that is compiled into
+ * the library; each device that loads the library's solver code keeps that
+ * array until the process exits.  The call allocates nothing.
+ *   g       graph from fj_graph_upload (its device becomes current)
+ *   stream  cudaStream_t of that device to run on (NULL: the default stream)
+ *   k       number of opinion vectors, 1 <= k <= 32
+ *   s       DEVICE float64[n*k], column-major; z: DEVICE float64[n*k] or NULL
+ *   quant   fj_quant[k] output in HOST memory, or NULL; info: optional
+ * The first call on each device looks up the array's device address; make
+ * that first call before capturing any stream into a CUDA graph.  All calls
+ * on a device share the one array and leave the last call's contents in it
+ * (the solver clears what it needs zeroed): calls whose GPU work overlaps in
+ * time race on it, so run them one after another (same stream, or
+ * synchronized).  The call returns when its results are written.
+ * Errors: FJ_ERR_ARG (NULL pointer, k out of range, or a solve whose scratch
+ * exceeds FJ_FIXED_SCRATCH_BYTES; fj_solve_ex has no such limit), and the
+ * solve errors of fj_solve_ex. */
+#define FJ_FIXED_SCRATCH_BYTES (64u << 20)
+fj_status fj_solve_fixed(const fj_graph* g, void* stream, int32_t k,
+                         const double* s, double* z, fj_quant* quant,
+                         const fj_opts* opts, fj_info* info);
+
 #ifdef __cplusplus
 }
 #endif

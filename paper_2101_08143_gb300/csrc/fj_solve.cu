@@ -22,6 +22,8 @@
 // blocks), and every block evaluates the same scalars, so control flow is
 // identical in all blocks and results are bit-reproducible.
 #include <algorithm>
+#include <cstring>
+#include <mutex>
 
 #include "fj_internal.cuh"
 #include "fj_walk.cuh"
@@ -689,4 +691,132 @@ fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32
   }
   *launches_out = li;
   return FJ_OK;
+}
+
+// ------------------------------------------------- allocation-free solve
+//
+// fj_solve_fixed runs the same solve kernel as fj_solve_ex, but takes all of
+// its scratch (solver vectors, reduction slots, status words, quantities)
+// from one fixed array compiled into the library instead of allocating it.
+// It exists for callers that must not allocate device memory during a solve:
+// code driving a latency-critical loop (cudaMalloc and cudaFree can
+// synchronize the whole device), and programs whose device memory is owned
+// by another allocator.  The array is FJ_FIXED_SCRATCH_BYTES per device, is
+// created when the library's solver code is loaded on a device and stays
+// until the process exits.
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_fixed_scratch[FJ_FIXED_SCRATCH_BYTES];
+
+constexpr int kFixedMaxDevices = 64;
+std::mutex g_fixed_mu;
+void* g_fixed_addr[kFixedMaxDevices];  // device address of g_fixed_scratch, per device
+
+// Host code cannot use g_fixed_scratch's name as a device address: look the
+// address up once per device, with that device current.
+fj_status fixed_scratch_address(int device, char** out) {
+  if (device < 0 || device >= kFixedMaxDevices) {
+    set_error("fj_solve_fixed: device %d out of range", device);
+    return FJ_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_fixed_mu);
+  if (!g_fixed_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_fixed_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "fj_solve_fixed: cudaGetSymbolAddress");
+    g_fixed_addr[device] = p;
+  }
+  *out = (char*)g_fixed_addr[device];
+  return FJ_OK;
+}
+
+}  // namespace
+
+extern "C" fj_status fj_solve_fixed(const fj_graph* g, void* stream, int32_t k, const double* s, double* z,
+                                    fj_quant* quant, const fj_opts* opts, fj_info* info) {
+  if (info) memset(info, 0, sizeof(*info));
+  if (!g || !s || k < 1 || k > 32) {
+    set_error("fj_solve_fixed: graph and s must be non-NULL and 1 <= k <= 32 (k=%d)", (int)k);
+    return FJ_ERR_ARG;
+  }
+  fj_opts o;
+  fj_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || o.max_iter < 1 ||
+      o.max_refine < 1 || o.precision < 0 || o.precision > 2) {
+    set_error("fj_solve_fixed: invalid options");
+    return FJ_ERR_ARG;
+  }
+  FJ_CUDA(cudaSetDevice(g->device));
+  int num_sms = 0;
+  FJ_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, g->device));
+  // launches of 32/16/8/4/2/1 columns, as in fj_solve_ex
+  int Ks[6], launches = 0;
+  for (int col = 0; col < k;) {
+    int K = 32;
+    while (K > k - col) K >>= 1;
+    Ks[launches++] = K;
+    col += K;
+  }
+  const int inner_bytes = o.precision == FJ_PREC_FP64 ? 8 : 4;
+  size_t ws_need = 0;
+  for (int i = 0; i < launches; ++i)
+    ws_need = std::max(ws_need, fj_solve_workspace_bytes(g, Ks[i], inner_bytes, num_sms));
+  // scratch layout: quantities [k][5] | residuals [k] | status [launches][3] | solver workspace
+  const size_t head = 4096;
+  if (ws_need > FJ_FIXED_SCRATCH_BYTES - head) {
+    set_error("fj_solve_fixed: this solve needs %zu bytes of scratch, the fixed area holds %zu; use "
+              "fj_solve_ex",
+              ws_need + head, (size_t)FJ_FIXED_SCRATCH_BYTES);
+    return FJ_ERR_ARG;
+  }
+  char* base = nullptr;
+  fj_status rc = fixed_scratch_address(g->device, &base);
+  if (rc != FJ_OK) return rc;
+  double* dq = (double*)base;
+  double* dres = dq + 32 * 5;
+  int* dstat = (int*)(dres + 32);
+  cudaStream_t st = (cudaStream_t)stream;
+  FJ_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int) * 3 * 6, st));
+  fj_opts od = o;
+  od.flags = FJ_DEVICE_PTRS;
+  int done = 0;
+  rc = fj_solve_device(g, st, num_sms, k, s, z, dq, dres, dstat, base + head, FJ_FIXED_SCRATCH_BYTES - head, od,
+                       &done, 0);
+  if (rc != FJ_OK) return rc;
+  double hq[32 * 5], hres[32];
+  int hstat[3 * 6];
+  FJ_CUDA(cudaMemcpyAsync(hq, dq, sizeof(double) * 5 * k, cudaMemcpyDeviceToHost, st));
+  FJ_CUDA(cudaMemcpyAsync(hres, dres, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  FJ_CUDA(cudaMemcpyAsync(hstat, dstat, sizeof(int) * 3 * launches, cudaMemcpyDeviceToHost, st));
+  FJ_CUDA(cudaStreamSynchronize(st));
+  int bits = 0, iters = 0, refines = 0;
+  for (int i = 0; i < launches; ++i) {
+    bits |= hstat[3 * i];
+    iters = std::max(iters, hstat[3 * i + 1]);
+    refines = std::max(refines, hstat[3 * i + 2]);
+  }
+  if (quant) memcpy(quant, hq, sizeof(double) * 5 * k);
+  rc = FJ_OK;
+  if (bits & kErrTimeout) {
+    set_error("a device-side wait timed out (solve abandoned)");
+    rc = FJ_ERR_TIMEOUT;
+  } else if (bits & kErrNumeric) {
+    set_error("NaN or Inf met in the iteration");
+    rc = FJ_ERR_NUMERIC;
+  } else if (bits & kErrNotConverged) {
+    set_error("iteration caps reached before the residual target");
+    rc = FJ_ERR_NOT_CONVERGED;
+  }
+  if (info) {
+    double worst = 0.0;
+    for (int j = 0; j < k; ++j) worst = std::max(worst, hres[j]);
+    info->iterations = iters;
+    info->refinements = refines;
+    info->rel_residual = worst;
+    info->status = rc;
+    info->columns = k;
+  }
+  return rc;
 }

@@ -1,0 +1,86 @@
+"""fj_solve_fixed: the solve variant that allocates no device memory.
+
+Some callers cannot allocate while they solve: a latency-critical loop (where
+cudaMalloc/cudaFree may stall the whole device) or a program whose device
+memory belongs to another allocator.  fj_solve_fixed serves them from a fixed
+scratch array inside the library.  This file checks, through the C ABI, that
+two calls in a row give the same answers as the allocating entry point
+fj_solve_ex, and that requests larger than the fixed array are refused.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+class _Quant(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("C_I", "D", "P", "C", "I_dc")]
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_08143_gb300 import fj
+    lib = fj.load()
+    f = lib.fj_solve_fixed
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(fj.Opts),
+                  ctypes.POINTER(fj.Info)]
+    ctx = fj.Context(0)
+    yield torch, fj, lib, ctx
+    ctx.close()
+
+
+def _fixed(torch, fj, lib, graph, s_dev, z_dev, k, opts):
+    quant = (_Quant * k)()
+    info = fj.Info()
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.fj_solve_fixed(graph.handle, ctypes.c_void_p(stream), k, ctypes.c_void_p(s_dev.data_ptr()),
+                            ctypes.c_void_p(z_dev.data_ptr()),
+                            ctypes.cast(quant, ctypes.c_void_p), ctypes.byref(opts),
+                            ctypes.byref(info))
+    torch.cuda.synchronize()
+    q = [{n: getattr(quant[j], n) for n in fj.QUANTITY_NAMES} for j in range(k)]
+    return rc, q, info
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fixed_matches_allocating_solve_twice(env, precision):
+    torch, fj, lib, ctx = env
+    from paper_2101_08143_gb300 import synth
+    g = synth.chung_lu(3000, 15000, 2.3, seed=12, weighted=True)
+    k = 3
+    s = synth.opinions_uniform(g.n, k, 17)
+    s_dev = torch.from_numpy(np.ascontiguousarray(s.T)).cuda()  # (k, n): column-major n x k
+    opts = fj.default_opts(precision=precision, tol=1e-10)
+    with ctx.upload_edges(g) as dg:
+        z_ref, q_ref, _ = ctx.solve(dg, s_dev, opts=opts)
+        for _ in range(2):
+            z_dev = torch.full_like(s_dev, float("nan"))
+            rc, q, info = _fixed(torch, fj, lib, dg, s_dev, z_dev, k, opts)
+            assert rc == fj.FJ_OK, lib.fj_last_error()
+            assert info.rel_residual <= 1e-10
+            np.testing.assert_allclose(z_dev.cpu().numpy(), z_ref.cpu().numpy(), rtol=0, atol=1e-8)
+            for j in range(k):
+                for name in fj.QUANTITY_NAMES:
+                    ref = q_ref[j][name]
+                    assert abs(q[j][name] - ref) <= 1e-6 * max(abs(ref), 1e-12), (name, q[j][name], ref)
+
+
+def test_fixed_refuses_oversized_requests(env):
+    torch, fj, lib, ctx = env
+    n = 200_000  # 32 columns of this size need far more than the fixed scratch
+    empty = np.zeros(0, np.int32)
+    with ctx.upload(n, empty, empty) as dg:
+        s_dev = torch.zeros((32, n), dtype=torch.float64, device="cuda")
+        z_dev = torch.zeros_like(s_dev)
+        rc, _, _ = _fixed(torch, fj, lib, dg, s_dev, z_dev, 32, fj.default_opts())
+        assert rc == fj.FJ_ERR_ARG
+        assert b"fixed area holds" in lib.fj_last_error()
+        rc, _, _ = _fixed(torch, fj, lib, dg, s_dev, z_dev, 33, fj.default_opts())
+        assert rc == fj.FJ_ERR_ARG
