@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -41,6 +42,42 @@ void set_error(const char* fmt, ...) {
   vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
   g_last_error = buf;
+}
+
+namespace {
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxPoolDevices];
+}  // namespace
+
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaMallocAsync(p, bytes, st);
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t np;
+      e = cudaMemPoolCreate(&np, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+      g_pool[dev] = np;
+    }
+    pool = g_pool[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+void pool_trim(int device) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (device >= 0 && device < kMaxPoolDevices && g_pool[device]) cudaMemPoolTrimTo(g_pool[device], 0);
 }
 
 fj_status cuda_fail(cudaError_t e, const char* what) {
@@ -174,6 +211,7 @@ fj_status fj_destroy(fj_ctx* c) {
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own) cudaStreamDestroy(c->own);
+  pool_trim(c->device);
   delete c;
   return FJ_OK;
 }
@@ -225,9 +263,9 @@ fj_status fj_graph_upload(fj_ctx* c, int64_t n, int64_t m, const int32_t* src, c
   int32_t *ds = nullptr, *dd = nullptr;
   float* dw = nullptr;
   const size_t eb = (size_t)std::max<int64_t>(m, 1) * 4;
-  if (cudaMallocAsync(&ds, eb, c->stream) != cudaSuccess ||
-      cudaMallocAsync(&dd, eb, c->stream) != cudaSuccess ||
-      (w && cudaMallocAsync(&dw, eb, c->stream) != cudaSuccess)) {
+  if (malloc_async(&ds, eb, c->stream) != cudaSuccess ||
+      malloc_async(&dd, eb, c->stream) != cudaSuccess ||
+      (w && malloc_async(&dw, eb, c->stream) != cudaSuccess)) {
     cudaGetLastError();
     if (ds) cudaFreeAsync(ds, c->stream);
     if (dd) cudaFreeAsync(dd, c->stream);

@@ -23,7 +23,7 @@
 namespace fj {
 
 constexpr int kSortThreads = 512;
-constexpr int kSortItems = 16;  // items per thread per block chunk
+constexpr int kSortItems = 8;  // items per thread per block chunk
 constexpr int kSortChunk = kSortThreads * kSortItems;
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
@@ -101,8 +101,19 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t
   for (int i = threadIdx.x; i < 256; i += kSortThreads) hist[(int64_t)i * gridDim.x + blockIdx.x] = h[i];
 }
 
-// Stable scatter: inside a block, items are ranked in input order (rounds of
-// kSortThreads items; within a round by warp, then by lane).
+// Stable scatter of one chunk of kSortChunk items.  Items are ranked in
+// input order (rounds of kSortThreads items: by warp, then by lane), placed
+// in shared memory in digit order, and written out as one contiguous run per
+// digit, so that global stores are coalesced.
+struct ScatterSmem {
+  int32_t key[kSortChunk];
+  int32_t col[kSortChunk];
+  float val[kSortChunk];
+  int wcnt[kSortThreads / 32][256];
+  int run[256];
+  int start[256];
+};
+
 template <bool FROM_EDGES>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int64_t N, int shift,
                                                                 const int32_t* __restrict__ offs,
@@ -110,46 +121,89 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
                                                                 int32_t* __restrict__ ocol,
                                                                 float* __restrict__ oval) {
   constexpr int kW = kSortThreads / 32;
-  __shared__ int base[256];
-  __shared__ int tot[256];
-  __shared__ int wcnt[kW][256];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int i = tid; i < 256; i += kSortThreads) base[i] = offs[(int64_t)i * gridDim.x + blockIdx.x];
   const unsigned lt_mask = (1u << lane) - 1u;
   const int64_t cbase = (int64_t)blockIdx.x * kSortChunk;
-  for (int r0 = 0; r0 < kSortChunk; r0 += kSortThreads) {
-    const int64_t p = cbase + r0 + tid;
-    const bool valid = p < N;
-    int32_t key = 0, col = 0;
-    float val = 0.f;
-    if (valid) load_entry<FROM_EDGES>(s, p, key, col, val);
-    const int digit = valid ? ((key >> shift) & 255) : 256;
-    for (int j = lane; j < 256; j += 32) wcnt[warp][j] = 0;
+  const int cnt = (int)((N - cbase) < kSortChunk ? (N - cbase) : kSortChunk);
+  for (int i = tid; i < 256; i += kSortThreads) sm.run[i] = 0;
+  int32_t key[kSortItems], col[kSortItems];
+  float val[kSortItems];
+  int rank[kSortItems];
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int li = r * kSortThreads + tid;
+    const bool valid = li < cnt;
+    key[r] = 0;
+    col[r] = 0;
+    val[r] = 0.f;
+    if (valid) load_entry<FROM_EDGES>(s, cbase + li, key[r], col[r], val[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const bool valid = r * kSortThreads + tid < cnt;
+    const int digit = valid ? ((key[r] >> shift) & 255) : 256;
+    for (int j = lane; j < 256; j += 32) sm.wcnt[warp][j] = 0;
     __syncwarp();
     const unsigned peers = __match_any_sync(kFull, digit);
-    const int rank = __popc(peers & lt_mask);
-    if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
+    const int rk = __popc(peers & lt_mask);
+    if (valid && rk == 0) sm.wcnt[warp][digit] = __popc(peers);
     __syncthreads();
     if (tid < 256) {
-      int run = 0;
+      int acc = sm.run[tid];
 #pragma unroll
       for (int w = 0; w < kW; ++w) {
-        const int c = wcnt[w][tid];
-        wcnt[w][tid] = run;
-        run += c;
+        const int c = sm.wcnt[w][tid];
+        sm.wcnt[w][tid] = acc;
+        acc += c;
       }
-      tot[tid] = run;
+      sm.run[tid] = acc;
     }
     __syncthreads();
-    if (valid) {
-      const int pos = base[digit] + wcnt[warp][digit] + rank;
-      okey[pos] = key;
-      ocol[pos] = col;
-      if (oval) oval[pos] = val;
+    rank[r] = valid ? sm.wcnt[warp][digit] + rk : 0;
+    __syncthreads();
+  }
+  // chunk-local start of every digit: exclusive scan of the 256 counts
+  if (warp == 0) {
+    int v[8], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      v[q] = sm.run[lane * 8 + q];
+      sum += v[q];
     }
-    __syncthreads();
-    if (tid < 256) base[tid] += tot[tid];
-    __syncthreads();
+    int incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, off);
+      if (lane >= off) incl += y;
+    }
+    int excl = incl - sum;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      sm.start[lane * 8 + q] = excl;
+      excl += v[q];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    if (r * kSortThreads + tid < cnt) {
+      const int digit = (key[r] >> shift) & 255;
+      const int pos = sm.start[digit] + rank[r];
+      sm.key[pos] = key[r];
+      sm.col[pos] = col[r];
+      sm.val[pos] = val[r];
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < cnt; i += kSortThreads) {
+    const int32_t k = sm.key[i];
+    const int digit = (k >> shift) & 255;
+    const int64_t pos = (int64_t)offs[(int64_t)digit * gridDim.x + blockIdx.x] + (i - sm.start[digit]);
+    okey[pos] = k;
+    ocol[pos] = sm.col[i];
+    if (oval) oval[pos] = sm.val[i];
   }
 }
 
@@ -229,7 +283,7 @@ static fj_status exclusive_scan(T* data, int64_t cnt, cudaStream_t st) {
     return FJ_OK;
   }
   T* sums = nullptr;
-  FJ_CUDA(cudaMallocAsync(&sums, blocks * sizeof(T), st));
+  FJ_CUDA(malloc_async(&sums, blocks * sizeof(T), st));
   count_launches(1);
   k_scan_reduce<T><<<(unsigned)blocks, kScanThreads, 0, st>>>(data, cnt, sums);
   fj_status rc = exclusive_scan<T>(sums, blocks, st);
@@ -257,41 +311,10 @@ __global__ void k_row_ptr(const int32_t* __restrict__ key, int64_t N, int64_t n,
   }
 }
 
-__global__ void k_tile_rows(const int32_t* __restrict__ row_ptr, int64_t n, int64_t nnz,
-                            int64_t n_tiles, int32_t* __restrict__ tile_row) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= n_tiles;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t d = t * kTileItems;
-    if (d > n + nnz) d = n + nnz;
-    tile_row[t] = (int32_t)merge_path_row(row_ptr, n, d);
-  }
-}
-
 __global__ void k_dinv_unit(const int32_t* __restrict__ row_ptr, int64_t n, float* __restrict__ dinv) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double d = (double)(row_ptr[i + 1] - row_ptr[i]);
-    dinv[i] = (float)(1.0 / (1.0 + d));
-  }
-}
-
-constexpr int kWalkWarps = 8;
-
-__global__ void __launch_bounds__(kWalkWarps * 32) k_row_sums(WalkGraph g, double* __restrict__ out,
-                                                              int32_t* __restrict__ wc_row,
-                                                              double* __restrict__ wc_val) {
-  __shared__ TileSmem sm[kWalkWarps];
-  const int warp = threadIdx.x >> 5;
-  const int64_t wg = (int64_t)blockIdx.x * kWalkWarps + warp;
-  walk_tiles<double, 1, kRowSum>(g, nullptr, out, wc_row, wc_val, wg, (void*)&sm[warp]);
-}
-
-__global__ void k_dinv_weighted(WalkGraph g, const double* __restrict__ sums,
-                                const double* __restrict__ wc_val, float* __restrict__ dinv) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double d = row_total<double, 1>(i, sums[i], g.row_ptr, wc_val, g.items_per_warp, 0);
-    dinv[i] = (float)(1.0 / (1.0 + d));
+    dinv[i] = __frcp_rn(1.0f + (float)(row_ptr[i + 1] - row_ptr[i]));
   }
 }
 
@@ -324,57 +347,84 @@ __global__ void k_apply_perm(const int32_t* __restrict__ perm, const int32_t* __
 }
 
 // Entry p of the row-sorted input CSR moves to its place in the solver-order
-// CSR (same position inside its row), with the column renumbered.
+// CSR (same position inside its row), with the column renumbered; entries
+// of short rows also go to their sliced-ELL position.
 __global__ void k_copy_entries(const int32_t* __restrict__ key, const int32_t* __restrict__ col_old,
-                               const float* __restrict__ val_old, int64_t nnz,
+                               const float* __restrict__ val_old, int64_t n,
                                const int32_t* __restrict__ row_ptr_old, const int32_t* __restrict__ old2new,
                                const int32_t* __restrict__ row_ptr_new, int32_t* __restrict__ col_new,
-                               float* __restrict__ val_new) {
+                               float* __restrict__ val_new, const int64_t* __restrict__ cnt,
+                               const int64_t* __restrict__ slice_off, int32_t* __restrict__ sell_col,
+                               float* __restrict__ sell_val) {
+  const int64_t nnz = row_ptr_old[n];  // entries past nnz are self-loops (key n)
+  const int64_t n_long = cnt[0];
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int32_t ro = key[p];
     const int32_t o = (int32_t)p - row_ptr_old[ro];
-    const int32_t pn = row_ptr_new[old2new[ro]] + o;
-    col_new[pn] = old2new[col_old[p]];
-    if (val_new) val_new[pn] = val_old[p];
+    const int32_t rn = old2new[ro];
+    const int32_t pn = row_ptr_new[rn] + o;
+    const int32_t c = old2new[col_old[p]];
+    const float w = val_old ? val_old[p] : 1.0f;
+    col_new[pn] = c;
+    if (val_new) val_new[pn] = w;
+    if (rn >= n_long) {
+      const int64_t sr = rn - n_long;
+      const int64_t pos = slice_off[sr >> 5] + 32 * (int64_t)o + (sr & 31);
+      sell_col[pos] = c;
+      if (sell_val) sell_val[pos] = w;
+    }
   }
 }
 
-// n_long = number of rows with more than kSellMaxLen entries (they come
-// first in solver order).
+// out[0] = n_long, the number of rows with more than kSellMaxLen entries;
+// out[1] = n_nz, the number of rows with at least one entry (in solver order
+// both are prefixes of the rows).
 __global__ void k_count_long(const int32_t* __restrict__ row_ptr, int64_t n, int64_t* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const bool lng = row_ptr[i + 1] - row_ptr[i] > kSellMaxLen;
-    const bool next = (i + 1 < n) && (row_ptr[i + 2] - row_ptr[i + 1] > kSellMaxLen);
-    if (lng && !next) out[0] = i + 1;
+    const int32_t d = row_ptr[i + 1] - row_ptr[i];
+    const int32_t dn = (i + 1 < n) ? row_ptr[i + 2] - row_ptr[i + 1] : 0;
+    if (d > kSellMaxLen && dn <= kSellMaxLen) out[0] = i + 1;
+    if (d > 0 && dn == 0) out[1] = i + 1;
   }
 }
 
-// slice_off[s] = 32 * (length of the slice's first, i.e. longest, row);
-// long_first[r] = number of chunks of long row r (both scanned afterwards).
-__global__ void k_layout_sizes(const int32_t* __restrict__ row_ptr, int64_t n, int64_t n_long,
-                               int64_t n_slices, int64_t* __restrict__ slice_off,
+// Device-side sizes of the layout (cnt[0], cnt[1] from k_count_long):
+//   cnt[0] n_long, cnt[1] n_nz, cnt[2] n_slices, cnt[3] nnz
+// slice_off[s] = 32 * (length of the slice's first, i.e. longest, row) and
+// long_first[r] = number of chunks of long row r (both scanned afterwards);
+// entries past the live counts are 0 so that scans over upper bounds work.
+__global__ void k_layout_sizes(const int32_t* __restrict__ row_ptr, int64_t n, int64_t* __restrict__ cnt,
+                               int64_t ns_cap, int64_t nl_cap, int64_t* __restrict__ slice_off,
                                int32_t* __restrict__ long_first) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n_slices + n_long;
+  const int64_t n_long = cnt[0];
+  const int64_t n_nz = cnt[1] > n_long ? cnt[1] : n_long;
+  const int64_t n_slices = (n_nz - n_long + 31) / 32;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= ns_cap + nl_cap + 1;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (i < n_slices) {
-      const int64_t r = n_long + 32 * i;
-      slice_off[i] = 32 * (int64_t)(row_ptr[r + 1] - row_ptr[r]);
-    } else if (i == n_slices) {
-      slice_off[n_slices] = 0;
+    if (i == 0) {
+      cnt[2] = n_slices;
+      cnt[3] = row_ptr[n];
+    }
+    if (i <= ns_cap) {
+      slice_off[i] = (i < n_slices) ? 32 * (int64_t)(row_ptr[n_long + 32 * i + 1] - row_ptr[n_long + 32 * i]) : 0;
     } else {
-      const int64_t r = i - n_slices - 1;
+      const int64_t r = i - ns_cap - 1;  // r in [0, nl_cap]
       long_first[r] = (r < n_long) ? (row_ptr[r + 1] - row_ptr[r] + kChunkLen - 1) / kChunkLen : 0;
     }
   }
 }
 
-// Fills the chunk table and the work-unit costs (chunks, then slices).
-__global__ void k_units(const int32_t* __restrict__ row_ptr, int64_t n_long, const int32_t* __restrict__ long_first,
-                        int64_t n_chunks, const int64_t* __restrict__ slice_off, int64_t n_slices,
-                        int32_t* __restrict__ chunk_row, int32_t* __restrict__ chunk_begin,
+// Fills the chunk table and the work-unit costs: unit_cost[c] for chunk c,
+// unit_cost[n_chunks + s] for slice s, 0 beyond (the array is sized by an
+// upper bound and scanned over all of it).
+__global__ void k_units(const int32_t* __restrict__ row_ptr, const int64_t* __restrict__ cnt,
+                        const int32_t* __restrict__ long_first, const int64_t* __restrict__ slice_off,
+                        int64_t units_cap, int32_t* __restrict__ chunk_row, int32_t* __restrict__ chunk_begin,
                         int32_t* __restrict__ chunk_end, int64_t* __restrict__ unit_cost) {
+  const int64_t n_long = cnt[0], n_slices = cnt[2];
+  const int64_t n_chunks = long_first[n_long];
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_long;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int32_t b = row_ptr[r], e = row_ptr[r + 1];
@@ -387,17 +437,20 @@ __global__ void k_units(const int32_t* __restrict__ row_ptr, int64_t n_long, con
       unit_cost[c] = (ce - cb) + 16;
     }
   }
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s <= n_slices;
-       s += (int64_t)gridDim.x * blockDim.x) {
-    unit_cost[n_chunks + s] = (s < n_slices) ? (slice_off[s + 1] - slice_off[s]) + 32 : 0;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u <= units_cap;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    if (u < n_chunks) continue;
+    const int64_t s = u - n_chunks;
+    unit_cost[u] = (s < n_slices) ? (slice_off[s + 1] - slice_off[s]) + 32 : 0;
   }
 }
 
 // Sliced ELL padding: positions past a row's length get col = the row itself
 // (w (x_r - x_r) = 0 for any weight) and weight 0.  One warp per slice.
-__global__ void k_sell_pad(const int32_t* __restrict__ row_ptr, int64_t n, int64_t n_long, int64_t n_slices,
+__global__ void k_sell_pad(const int32_t* __restrict__ row_ptr, int64_t n, const int64_t* __restrict__ cnt,
                            const int64_t* __restrict__ slice_off, int32_t* __restrict__ sell_col,
                            float* __restrict__ sell_val) {
+  const int64_t n_long = cnt[0], n_slices = cnt[2];
   const int lane = threadIdx.x & 31;
   for (int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; s < n_slices;
        s += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -412,24 +465,73 @@ __global__ void k_sell_pad(const int32_t* __restrict__ row_ptr, int64_t n, int64
   }
 }
 
-// Sliced ELL entries of the short rows, from the solver-order CSR.  One
-// thread per entry; row lookup by the entry's row in the input CSR.
-__global__ void k_sell_fill(const int32_t* __restrict__ key, int64_t nnz, const int32_t* __restrict__ row_ptr_old,
-                            const int32_t* __restrict__ old2new, const int32_t* __restrict__ row_ptr_new,
-                            const int32_t* __restrict__ col_new, const float* __restrict__ val_new,
-                            int64_t n_long, const int64_t* __restrict__ slice_off, int32_t* __restrict__ sell_col,
-                            float* __restrict__ sell_val) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t ro = key[p];
-    const int32_t rn = old2new[ro];
-    if (rn < n_long) continue;
-    const int32_t o = (int32_t)p - row_ptr_old[ro];
-    const int32_t pn = row_ptr_new[rn] + o;
-    const int64_t sr = rn - n_long;
-    const int64_t pos = slice_off[sr >> 5] + 32 * (int64_t)o + (sr & 31);
-    sell_col[pos] = col_new[pn];
-    if (sell_val) sell_val[pos] = val_new[pn];
+// Weighted degrees, accumulated in float32 in a fixed order (the Jacobi
+// preconditioner needs no more).  Long rows: a warp per chunk sums its
+// entries (lane-strided, then an xor tree) ...
+__global__ void k_chunk_wsum(const float* __restrict__ val, const int32_t* __restrict__ long_first,
+                             const int64_t* __restrict__ cnt, const int32_t* __restrict__ chunk_begin,
+                             const int32_t* __restrict__ chunk_end, float* __restrict__ part) {
+  const int64_t n_chunks = long_first[cnt[0]];
+  const int lane = threadIdx.x & 31;
+  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < n_chunks;
+       c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t e = chunk_end[c];
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    int32_t p = chunk_begin[c] + lane;
+    for (; p + 96 < e; p += 128) {
+      a[0] += val[p];
+      a[1] += val[p + 32];
+      a[2] += val[p + 64];
+      a[3] += val[p + 96];
+    }
+    for (; p < e; p += 32) a[0] += val[p];
+    float d = (a[0] + a[1]) + (a[2] + a[3]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(kFull, d, off);
+    if (lane == 0) part[c] = d;
+  }
+}
+
+// ... then a warp per long row adds its chunk sums, and a thread per short
+// row walks its sliced-ELL positions in order.  dinv_i = 1 / (1 + d_i).
+__global__ void k_dinv_weighted(const int32_t* __restrict__ row_ptr, int64_t n, const int64_t* __restrict__ cnt,
+                                const int32_t* __restrict__ long_first, const float* __restrict__ part,
+                                const int64_t* __restrict__ slice_off, const float* __restrict__ sell_val,
+                                float* __restrict__ dinv) {
+  const int64_t n_long = cnt[0], n_nz = cnt[1] > cnt[0] ? cnt[1] : cnt[0];
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = gw; r < n_long; r += nw) {
+    float d = 0.0f;
+    for (int32_t c = long_first[r] + lane; c < long_first[r + 1]; c += 32) d += part[c];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(kFull, d, off);
+    if (lane == 0) dinv[r] = __frcp_rn(1.0f + d);
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n - n_long;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = n_long + i;
+    float d = 0.0f;
+    if (row < n_nz) {
+      const int32_t len = row_ptr[row + 1] - row_ptr[row];
+      const float* __restrict__ v = sell_val + slice_off[i >> 5] + (i & 31);
+      for (int32_t p = 0; p < len; ++p) d += v[32 * p];
+    }
+    dinv[row] = __frcp_rn(1.0f + d);
+  }
+}
+
+// Merge-path row coordinate of every tile start, for nnz read on the device.
+__global__ void k_tile_rows_dev(const int32_t* __restrict__ row_ptr, int64_t n, int64_t tiles_cap,
+                                int32_t* __restrict__ tile_row) {
+  const int64_t nnz = row_ptr[n];
+  const int64_t n_tiles = (n + nnz + kTileItems - 1) / kTileItems;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= tiles_cap && t <= n_tiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t d = t * kTileItems;
+    if (d > n + nnz) d = n + nnz;
+    tile_row[t] = (int32_t)merge_path_row(row_ptr, n, d);
   }
 }
 
@@ -454,7 +556,7 @@ static fj_status radix_sort(EntrySrc src, bool from_edges, int64_t N, int64_t ke
   *result = 0;
   if (N == 0) return FJ_OK;
   int32_t* h = nullptr;
-  FJ_CUDA(cudaMallocAsync(&h, 256 * nblocks * sizeof(int32_t), st));
+  FJ_CUDA(malloc_async(&h, 256 * nblocks * sizeof(int32_t), st));
   fj_status rc = FJ_OK;
   for (int pass = 0; pass < passes && rc == FJ_OK; ++pass) {
     const bool edges = from_edges && pass == 0;
@@ -473,11 +575,14 @@ static fj_status radix_sort(EntrySrc src, bool from_edges, int64_t N, int64_t ke
     }
     rc = exclusive_scan<int32_t>(h, 256 * nblocks, st);
     if (rc != FJ_OK) break;
+    const size_t ssm = sizeof(ScatterSmem);
     if (edges) {
-      k_radix_scatter<true><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, 0, h, kb[dstb], cb[dstb], vb[dstb]);
+      cudaFuncSetAttribute(k_radix_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+      k_radix_scatter<true><<<(unsigned)nblocks, kSortThreads, ssm, st>>>(s, N, 0, h, kb[dstb], cb[dstb], vb[dstb]);
     } else {
-      k_radix_scatter<false><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, pass * 8, h, kb[dstb], cb[dstb],
-                                                                         vb[dstb]);
+      cudaFuncSetAttribute(k_radix_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+      k_radix_scatter<false><<<(unsigned)nblocks, kSortThreads, ssm, st>>>(s, N, pass * 8, h, kb[dstb], cb[dstb],
+                                                                          vb[dstb]);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "radix sort");
@@ -503,7 +608,7 @@ struct Pool {
   template <typename T>
   T* get(int64_t count) {
     void* p = nullptr;
-    if (cudaMallocAsync(&p, (size_t)std::max<int64_t>(count, 1) * sizeof(T), st) != cudaSuccess) {
+    if (malloc_async(&p, (size_t)std::max<int64_t>(count, 1) * sizeof(T), st) != cudaSuccess) {
       cudaGetLastError();
       failed = true;
       return nullptr;
@@ -620,7 +725,7 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   pool.keep(perm);
   int32_t* old2new = pool.get<int32_t>(n);
   g->row_ptr = (int32_t*)nullptr;
-  if (cudaMallocAsync(&g->row_ptr, (n + 1) * sizeof(int32_t), st) != cudaSuccess || !old2new) {
+  if (malloc_async(&g->row_ptr, (n + 1) * sizeof(int32_t), st) != cudaSuccess || !old2new) {
     cudaGetLastError();
     g->row_ptr = nullptr;
     return fail(oom());
@@ -630,108 +735,93 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   rc = exclusive_scan<int32_t>(g->row_ptr, n + 1, st);
   if (rc != FJ_OK) return fail(rc);
 
-  // ---- 3. solver-order CSR
-  int32_t nnz32 = 0;
-  if (cudaMemcpyAsync(&nnz32, g->row_ptr + n, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return fail(FJ_ERR_CUDA);
-  const int64_t nnz = nnz32;
-  g->nnz = nnz;
-  if (cudaMallocAsync(&g->col, (nnz + kPad) * 4, st) != cudaSuccess ||
-      (weighted && cudaMallocAsync(&g->val, (nnz + kPad) * 4, st) != cudaSuccess)) {
+  // ---- 3. layout of long rows, slices, chunk table and work units, from
+  // the degrees alone.  Sizes stay on the device; buffers use upper bounds:
+  // in decreasing-degree order a slice's first row is no longer than any row
+  // of the slice before it, so the sliced ELL holds at most
+  // nnz + 32 * kSellMaxLen entries.
+  const int64_t nl_cap = std::min<int64_t>(n, N / (kSellMaxLen + 1));
+  const int64_t ns_cap = (n + 31) / 32;
+  const int64_t nc_cap = nl_cap + N / kChunkLen + 1;
+  const int64_t units_cap = nc_cap + ns_cap;
+  const int64_t sell_cap = N + 32 * kSellMaxLen;
+  int64_t* dcnt = pool.get<int64_t>(8);
+  if (!dcnt) return fail(oom());
+  cudaMemsetAsync(dcnt, 0, 64, st);
+  if (malloc_async(&g->col, (N + kPad) * 4, st) != cudaSuccess ||
+      (weighted && malloc_async(&g->val, (N + kPad) * 4, st) != cudaSuccess) ||
+      malloc_async(&g->slice_off, (ns_cap + 1) * 8, st) != cudaSuccess ||
+      malloc_async(&g->long_first, (nl_cap + 1) * 4, st) != cudaSuccess ||
+      malloc_async(&g->sell_col, (sell_cap + kPad) * 4, st) != cudaSuccess ||
+      (weighted && malloc_async(&g->sell_val, (sell_cap + kPad) * 4, st) != cudaSuccess) ||
+      malloc_async(&g->chunk_row, nc_cap * 4, st) != cudaSuccess ||
+      malloc_async(&g->chunk_begin, nc_cap * 4, st) != cudaSuccess ||
+      malloc_async(&g->chunk_end, nc_cap * 4, st) != cudaSuccess ||
+      malloc_async(&g->unit_prefix, (units_cap + 1) * 8, st) != cudaSuccess) {
     cudaGetLastError();
     return fail(oom());
   }
-  cudaMemsetAsync(g->col + nnz, 0, kPad * 4, st);
-  if (weighted) cudaMemsetAsync(g->val + nnz, 0, kPad * 4, st);
-  count_launches(1);
-  k_copy_entries<<<grid_for(nnz, 256), 256, 0, st>>>(key_old, col_old, val_old, nnz, rp_old, old2new,
-                                                     g->row_ptr, g->col, g->val);
-  if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
-
-  // ---- 4. long rows, slices, chunk table, work units
-  int64_t* scal = pool.get<int64_t>(2);
-  if (!scal) return fail(oom());
-  cudaMemsetAsync(scal, 0, 16, st);
-  count_launches(1);
-  k_count_long<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, scal);
-  int64_t n_long = 0;
-  if (cudaMemcpyAsync(&n_long, scal, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return fail(FJ_ERR_CUDA);
-  g->n_long = n_long;
-  g->n_slices = (n - n_long + 31) / 32;
-  if (cudaMallocAsync(&g->slice_off, (g->n_slices + 1) * 8, st) != cudaSuccess ||
-      cudaMallocAsync(&g->long_first, (n_long + 1) * 4, st) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(oom());
-  }
-  count_launches(1);
-  k_layout_sizes<<<grid_for(g->n_slices + n_long + 1, 256), 256, 0, st>>>(g->row_ptr, n, n_long, g->n_slices,
-                                                                        g->slice_off, g->long_first);
-  rc = exclusive_scan<int64_t>(g->slice_off, g->n_slices + 1, st);
-  if (rc == FJ_OK) rc = exclusive_scan<int32_t>(g->long_first, n_long + 1, st);
+  cudaMemsetAsync(g->col, 0, (N + kPad) * 4, st);
+  if (weighted) cudaMemsetAsync(g->val, 0, (N + kPad) * 4, st);
+  count_launches(2);
+  k_count_long<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, dcnt);
+  k_layout_sizes<<<grid_for(ns_cap + nl_cap + 2, 256), 256, 0, st>>>(g->row_ptr, n, dcnt, ns_cap, nl_cap,
+                                                                    g->slice_off, g->long_first);
+  rc = exclusive_scan<int64_t>(g->slice_off, ns_cap + 1, st);
+  if (rc == FJ_OK) rc = exclusive_scan<int32_t>(g->long_first, nl_cap + 1, st);
   if (rc != FJ_OK) return fail(rc);
-  int64_t hs[2] = {0, 0};
-  int32_t hch = 0;
-  if (cudaMemcpyAsync(&hs[0], g->slice_off + g->n_slices, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaMemcpyAsync(&hch, g->long_first + n_long, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return fail(FJ_ERR_CUDA);
-  g->sell_nnz = hs[0];
-  g->n_chunks = hch;
-  g->n_units = g->n_chunks + g->n_slices;
-  if (cudaMallocAsync(&g->sell_col, (g->sell_nnz + kPad) * 4, st) != cudaSuccess ||
-      (weighted && cudaMallocAsync(&g->sell_val, (g->sell_nnz + kPad) * 4, st) != cudaSuccess) ||
-      cudaMallocAsync(&g->chunk_row, std::max<int64_t>(g->n_chunks, 1) * 4, st) != cudaSuccess ||
-      cudaMallocAsync(&g->chunk_begin, std::max<int64_t>(g->n_chunks, 1) * 4, st) != cudaSuccess ||
-      cudaMallocAsync(&g->chunk_end, std::max<int64_t>(g->n_chunks, 1) * 4, st) != cudaSuccess ||
-      cudaMallocAsync(&g->unit_prefix, (g->n_units + 1) * 8, st) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(oom());
-  }
   count_launches(3);
-  k_units<<<grid_for(std::max(n_long, g->n_slices + 1), 256), 256, 0, st>>>(
-      g->row_ptr, n_long, g->long_first, g->n_chunks, g->slice_off, g->n_slices, g->chunk_row, g->chunk_begin,
-      g->chunk_end, g->unit_prefix);
-  k_sell_pad<<<grid_for(g->n_slices * 32, 256), 256, 0, st>>>(g->row_ptr, n, n_long, g->n_slices, g->slice_off,
-                                                              g->sell_col, g->sell_val);
-  k_sell_fill<<<grid_for(nnz, 256), 256, 0, st>>>(key_old, nnz, rp_old, old2new, g->row_ptr, g->col, g->val,
-                                                  n_long, g->slice_off, g->sell_col, g->sell_val);
+  k_units<<<grid_for(std::max(nl_cap, units_cap + 1), 256), 256, 0, st>>>(
+      g->row_ptr, dcnt, g->long_first, g->slice_off, units_cap, g->chunk_row, g->chunk_begin, g->chunk_end,
+      g->unit_prefix);
+  k_sell_pad<<<grid_for(ns_cap * 32, 256), 256, 0, st>>>(g->row_ptr, n, dcnt, g->slice_off, g->sell_col,
+                                                         g->sell_val);
+  // ---- 4. entries to the solver-order CSR and the sliced ELL
+  k_copy_entries<<<grid_for(N, 256), 256, 0, st>>>(key_old, col_old, val_old, n, rp_old, old2new, g->row_ptr,
+                                                   g->col, g->val, dcnt, g->slice_off, g->sell_col, g->sell_val);
   if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
-  rc = exclusive_scan<int64_t>(g->unit_prefix, g->n_units + 1, st);
+  rc = exclusive_scan<int64_t>(g->unit_prefix, units_cap + 1, st);
   if (rc != FJ_OK) return fail(rc);
 
   // ---- 5. merge-path tile plan and Jacobi preconditioner
-  g->n_tiles = (n + nnz + kTileItems - 1) / kTileItems;
-  if (cudaMallocAsync(&g->tile_row, (g->n_tiles + 1) * sizeof(int32_t), st) != cudaSuccess ||
-      cudaMallocAsync(&g->dinv, n * sizeof(float), st) != cudaSuccess) {
+  const int64_t tiles_cap = (n + N + kTileItems - 1) / kTileItems;
+  if (malloc_async(&g->tile_row, (tiles_cap + 1) * sizeof(int32_t), st) != cudaSuccess ||
+      malloc_async(&g->dinv, n * sizeof(float), st) != cudaSuccess) {
     cudaGetLastError();
     return fail(oom());
   }
-  count_launches(1);
-  k_tile_rows<<<grid_for(g->n_tiles + 1, 256), 256, 0, st>>>(g->row_ptr, n, nnz, g->n_tiles, g->tile_row);
-  if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
+  count_launches(2);
+  k_tile_rows_dev<<<grid_for(tiles_cap + 1, 256), 256, 0, st>>>(g->row_ptr, n, tiles_cap, g->tile_row);
   if (!weighted) {
-    count_launches(1);
     k_dinv_unit<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, g->dinv);
-    if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
   } else {
-    int64_t warps = g->n_tiles < 152 * 64 ? g->n_tiles : 152 * 64;
-    if (warps < 1) warps = 1;
-    WalkGraph wg{g->row_ptr, g->col, g->val, g->tile_row, n, nnz, g->n_tiles, 1, {}};
-    set_tiles_per_warp(wg, (g->n_tiles + warps - 1) / warps);
-    const int64_t blocks = (warps + kWalkWarps - 1) / kWalkWarps;
-    double* sums = pool.get<double>(n);
-    int32_t* wrow = pool.get<int32_t>(blocks * kWalkWarps);
-    double* wval = pool.get<double>(blocks * kWalkWarps);
-    if (pool.failed) return fail(oom());
+    float* cpart = pool.get<float>(nc_cap);
+    if (!cpart) return fail(oom());
     count_launches(2);
-    k_row_sums<<<(unsigned)blocks, kWalkWarps * 32, 0, st>>>(wg, sums, wrow, wval);
-    k_dinv_weighted<<<grid_for(n, 256), 256, 0, st>>>(wg, sums, wval, g->dinv);
-    if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
+    k_chunk_wsum<<<grid_for(nc_cap * 32, 256), 256, 0, st>>>(g->val, g->long_first, dcnt, g->chunk_begin,
+                                                             g->chunk_end, cpart);
+    k_dinv_weighted<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, dcnt, g->long_first, cpart, g->slice_off,
+                                                      g->sell_val, g->dinv);
   }
-  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(FJ_ERR_CUDA);
+  if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
+
+  // ---- sizes back to the host (the one round trip after validation)
+  int64_t hc[4] = {0, 0, 0, 0};
+  int32_t hch = 0;
+  if (cudaMemcpyAsync(hc, dcnt, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(FJ_ERR_CUDA);
+  if (cudaMemcpyAsync(&hch, g->long_first + hc[0], 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&g->sell_nnz, g->slice_off + hc[2], 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(FJ_ERR_CUDA);
+  g->n_long = hc[0];
+  g->n_nz = std::max(hc[1], hc[0]);
+  g->n_slices = hc[2];
+  g->nnz = hc[3];
+  g->n_chunks = hch;
+  g->n_units = g->n_chunks + g->n_slices;
+  g->n_tiles = (n + g->nnz + kTileItems - 1) / kTileItems;
   *out = g;
   return FJ_OK;
 }

@@ -9,7 +9,8 @@
 //   tile_row         merge-path row coordinate of every kTileItems tile
 //   rows [0, n_long) with more than kSellMaxLen entries ("long rows") are cut
 //                    into chunks of at most kChunkLen entries
-//   rows [n_long, n) are stored as sliced ELL: slices of 32 consecutive rows,
+//   rows [n_long, n_nz) are stored as sliced ELL (rows [n_nz, n) have no
+//                    entries): slices of 32 consecutive rows,
 //                    column-major inside a slice (entry p of the slice's lane
 //                    l at slice_off + 32 p + l), padded with col = own row
 //   unit_prefix      cumulative cost of the work units (chunks, then slices)
@@ -67,8 +68,9 @@ struct fj_graph {
   float* dinv;
   int32_t* tile_row;
   int32_t* perm;  // perm[i] = input id of solver node i
-  // long rows [0, n_long) in chunks
+  // long rows [0, n_long) in chunks; rows [n_nz, n) have no entries
   int64_t n_long;
+  int64_t n_nz;
   int64_t n_chunks;
   int32_t* long_first;   // [n_long + 1] first chunk of each long row
   int32_t* chunk_row;    // [n_chunks]
@@ -126,6 +128,16 @@ __device__ __forceinline__ int64_t merge_path_row(const int32_t* row_ptr,
 // ------------------------------------------------------------------- host
 
 namespace fj {
+// Stream-ordered allocation from the library's memory pool of the current
+// device.  The pool keeps freed memory for reuse (its release threshold is
+// unlimited), so repeated uploads and solves do not map and unmap pages.
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t st);
+// Returns the pool's unused memory to the system (fj_destroy).
+void pool_trim(int device);
+template <typename T>
+inline cudaError_t malloc_async(T** p, size_t bytes, cudaStream_t st) {
+  return pool_malloc_async(reinterpret_cast<void**>(p), bytes, st);
+}
 void set_error(const char* fmt, ...);
 // Counts kernel launches made by the library (all contexts, this process).
 void count_launches(int k);

@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
           sb = P.sbar[idx];
           qv = P.q[idx];
           if (kSell)
-            lq = P.t64[idx];
+            lq = i < P.sg.n_nz ? P.t64[idx] : 0.0;
           else
             lq = row_total<double, K>(i, P.t64[idx], P.g.row_ptr, P.wc_val64, P.g.items_per_warp, c);
         }
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
             if (idx < NK) {
               const int64_t i = idx / K;
               uv[e] = vu[idx];
-              tv[e] = kSell ? vt[idx]
+              tv[e] = kSell ? (i < P.sg.n_nz ? vt[idx] : VI(0))
                             : row_total<VI, K>(i, vt[idx], P.g.row_ptr, P.wc_val, P.g.items_per_warp, c);
               pv[e] = fst ? VI(0) : vp[idx];
               dv[e] = fst ? VI(0) : vd[idx];
@@ -581,8 +581,8 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   set_tiles_per_warp(P.g, tpw);
   P.sg = SellGraph{g->row_ptr,   g->col,       g->val,      g->long_first, g->chunk_row,
                    g->chunk_begin, g->chunk_end, g->slice_off, g->sell_col,   g->sell_val,
-                   g->unit_prefix, n,            g->n_long,   g->n_chunks,   g->n_slices,
-                   g->n_units};
+                   g->unit_prefix, n,            g->n_long,   g->n_nz,       g->n_chunks,
+                   g->n_slices,    g->n_units};
   P.perm = g->perm;
   P.dinv = g->dinv;
   P.s = s;

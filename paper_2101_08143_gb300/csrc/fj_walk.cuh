@@ -313,6 +313,7 @@ struct SellGraph {
   const int64_t* unit_prefix;
   int64_t n;
   int64_t n_long;
+  int64_t n_nz;  // rows [n_nz, n) have no entries: their sums are 0
   int64_t n_chunks;
   int64_t n_slices;
   int64_t n_units;
