@@ -58,7 +58,7 @@ struct SolveParams {
   SellGraph sg;  // sliced-ELL view (K <= 4)
   const int32_t* perm;  // solver node -> input id
   VI* hub_part;         // [n_chunks][K] chunk sums of multi-chunk rows
-  double* hub_part64;
+  df64* hub_part64;
   int* hub_cnt;         // [n_long] finished chunks per long row
   const float* dinv;
   // problem (column c of this launch: s + c*ld)
@@ -68,10 +68,10 @@ struct SolveParams {
   double* quant;  // [K][5]
   double* resid;  // [K]
   int* status;    // [0] err bits, [1] iterations, [2] refinements
-  // row-major n x K workspace
-  double* sbar;
-  double* q;
-  double* t64;
+  // row-major n x K workspace; the refinement state is double-float
+  df64* sbar;
+  df64* q;
+  df64* t64;
   VI* x;
   VI* r;
   VI* u;
@@ -80,7 +80,7 @@ struct SolveParams {
   VI* t;
   int32_t* wc_row;
   VI* wc_val;
-  double* wc_val64;
+  df64* wc_val64;
   double* part;  // [gridDim][NSLOT][K]
   Barrier* bar;
   // options
@@ -178,7 +178,7 @@ __device__ __forceinline__ double lane_share(T (&v)[K]) {
   double mine = 0.0;
 #pragma unroll
   for (int cc = 0; cc < K; ++cc) {
-    double x = (double)v[cc];
+    double x = to_double(v[cc]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(kFull, x, off);
     if (lane == cc) mine = x;
@@ -249,32 +249,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
     // r64 = s_bar - q - t64 (t64 = off-diagonal part of L q, from the walk)
     // plus the quantity partials and the start of the next inner solve.
     {
-      double a_rr64 = 0, a_p = 0, a_c = 0, a_ci = 0, a_bb = 0, a_gam = 0, a_rr = 0, a_uu = 0;
+      // float64-accurate sums in double-float; the inner-solve sums in VI
+      const df64 z0 = df_from_float(0.0f);
+      df64 a_rr64 = z0, a_p = z0, a_c = z0, a_ci = z0;
+      double a_bb = 0, a_gam = 0, a_rr = 0, a_uu = 0;
       const double m = mu[c];
+      const df64 mdf = df_from_double(m);
       for (int64_t idx = gtid; idx < NK; idx += gstride) {
         const int64_t i = idx / K;
-        double sb, qv, lq;
+        df64 sb, qv, lq;
         if (init) {
-          sb = P.s[(int64_t)c * P.ld + P.perm[i]] - m;
+          const double sbd = P.s[(int64_t)c * P.ld + P.perm[i]] - m;
+          sb = df_from_double(sbd);
           P.sbar[idx] = sb;
-          P.q[idx] = 0.0;
-          qv = 0.0;
-          lq = 0.0;
-          a_bb += sb * sb;
+          P.q[idx] = z0;
+          qv = z0;
+          lq = z0;
+          a_bb += sbd * sbd;
         } else {
           sb = P.sbar[idx];
           qv = P.q[idx];
           if (kSell)
-            lq = i < P.sg.n_nz ? P.t64[idx] : 0.0;
+            lq = i < P.sg.n_nz ? P.t64[idx] : z0;
           else
-            lq = row_total<double, K>(i, P.t64[idx], P.g.row_ptr, P.wc_val64, P.g.items_per_warp, c);
+            lq = row_total<df64, K>(i, P.t64[idx], P.g.row_ptr, P.wc_val64, P.g.items_per_warp, c);
         }
-        const double r64 = sb - qv - lq;
-        a_rr64 += r64 * r64;
-        a_p += qv * qv;
-        a_c += (qv + m) * (qv + m);
-        a_ci += (sb - qv) * (sb - qv);
-        const VI rv = (VI)r64;
+        const df64 r64 = df_sub(df_sub(sb, qv), lq);
+        a_rr64 += df_mul(r64, r64);
+        a_p += df_mul(qv, qv);
+        const df64 zq = df_add(qv, mdf);
+        a_c += df_mul(zq, zq);
+        const df64 dq = df_sub(sb, qv);
+        a_ci += df_mul(dq, dq);
+        const VI rv = (VI)r64.hi + (VI)r64.lo;
         const VI uv = P.dinv[i] * rv;
         P.x[idx] = VI(0);
         P.r[idx] = rv;
@@ -283,7 +290,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         a_rr += (double)(rv * rv);
         a_uu += (double)(uv * uv);
       }
-      const double v[7] = {a_rr64, a_p, a_c, a_ci, a_gam, a_rr, a_uu};
+      const double v[7] = {df_to_double(a_rr64), df_to_double(a_p), df_to_double(a_c), df_to_double(a_ci),
+                           a_gam, a_rr, a_uu};
       const int sl[7] = {S_RR64, S_P, S_C, S_CI, S_GAM, S_RR, S_UU};
       block_store<K, 7>(v, sl, P.part, red);
       if (init) {
@@ -501,19 +509,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       __syncthreads();
     }
 
-    // q += x (float64), then the residual walk t64 = L q and sum w (q_i-q_j)^2
-    for (int64_t idx = gtid; idx < NK; idx += gstride) P.q[idx] += (double)P.x[idx];
+    // q += x (double-float), then the residual walk t64 = L q and
+    // sum w (q_i - q_j)^2
+    for (int64_t idx = gtid; idx < NK; idx += gstride) {
+      if constexpr (sizeof(VI) == 4)
+        P.q[idx] = df_add_f(P.q[idx], (float)P.x[idx]);
+      else
+        P.q[idx] = df_add(P.q[idx], df_from_double((double)P.x[idx]));
+    }
     if (!grid_sync(P.bar, status, epoch)) return;
     {
       double quad;
       if constexpr (kSell) {
-        double qd[K];
+        df64 qd[K];
 #pragma unroll
-        for (int cc = 0; cc < K; ++cc) qd[cc] = 0.0;
-        sell_walk<double, K>(P.sg, P.q, P.t64, P.hub_part64, P.hub_cnt, u0, u1, qd);
-        quad = lane_share<double, K>(qd);
+        for (int cc = 0; cc < K; ++cc) qd[cc] = df_from_float(0.0f);
+        sell_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, P.hub_cnt, u0, u1, qd);
+        quad = lane_share<df64, K>(qd);
       } else {
-        quad = walk_tiles<double, K, kLap>(P.g, P.q, P.t64, P.wc_row, P.wc_val64, wg, my_tsm);
+        quad = df_to_double(walk_tiles<df64, K, kLap>(P.g, P.q, P.t64, P.wc_row, P.wc_val64, wg, my_tsm));
       }
       const double v[1] = {quad};
       const int sl[1] = {S_D};
@@ -525,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   // ---------------------------------------------------------------- output
   if (P.z_out) {
     for (int64_t idx = gtid; idx < NK; idx += gstride)
-      P.z_out[(int64_t)c * P.ld + P.perm[idx / K]] = P.q[idx] + mu[c];
+      P.z_out[(int64_t)c * P.ld + P.perm[idx / K]] = df_to_double(P.q[idx]) + mu[c];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     int all_done = 1;
@@ -591,9 +605,9 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.quant = quant;
   P.resid = resid;
   P.status = status;
-  P.sbar = (double*)take(NK * 8);
-  P.q = (double*)take(NK * 8);
-  P.t64 = (double*)take(NK * 8);
+  P.sbar = (df64*)take(NK * 8);
+  P.q = (df64*)take(NK * 8);
+  P.t64 = (df64*)take(NK * 8);
   P.x = (VI*)take(NK * sizeof(VI));
   P.r = (VI*)take(NK * sizeof(VI));
   P.u = (VI*)take(NK * sizeof(VI));
@@ -602,10 +616,10 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.t = (VI*)take(NK * sizeof(VI));
   P.wc_row = (int32_t*)take(warps * 4);
   P.wc_val = (VI*)take(warps * K * sizeof(VI));
-  P.wc_val64 = (double*)take(warps * K * 8);
+  P.wc_val64 = (df64*)take(warps * K * 8);
   P.part = (double*)take((size_t)blocks * NSLOT * K * 8);
   P.hub_part = (VI*)take(std::max<int64_t>(g->n_chunks, 1) * K * sizeof(VI));
-  P.hub_part64 = (double*)take(std::max<int64_t>(g->n_chunks, 1) * K * 8);
+  P.hub_part64 = (df64*)take(std::max<int64_t>(g->n_chunks, 1) * K * 8);
   P.hub_cnt = (int*)take(std::max<int64_t>(g->n_long, 1) * 4);
   P.bar = (Barrier*)take(sizeof(Barrier));
   if (off > ws_bytes) {

@@ -19,6 +19,9 @@
 // The result is bit-reproducible for a fixed graph and launch shape.
 #pragma once
 
+#include <type_traits>
+
+#include "fj_df64.cuh"
 #include "fj_internal.cuh"
 
 namespace fj {
@@ -117,14 +120,14 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
   const int64_t t_begin = wg * g.tiles_per_warp;
   int64_t t_end = t_begin + g.tiles_per_warp;
   if (t_end > g.n_tiles) t_end = g.n_tiles;
-  T quad = T(0);
+  T quad = num<T>(0.f);
   if (t_begin >= t_end) return quad;
 
   // tile row coordinates of 32 tiles at a time live in one register per lane
   int32_t trow = g.tile_row[t_begin + (lane < t_end - t_begin + 1 ? lane : 0)];
   int64_t tbase = t_begin;
   int32_t carry_row = __shfl_sync(kFull, trow, 0);
-  T carry = T(0);
+  T carry = num<T>(0.f);
   for (int64_t t = t_begin; t < t_end; ++t) {
     if (t + 1 - tbase >= 32) {  // refill the coordinate window
       tbase = t;
@@ -182,13 +185,13 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
       for (int u = 0; u < kPer; ++u) {
         const int j = lane + 32 * u;
 #pragma unroll
-        for (int cc = 0; cc < K; ++cc) xg[u][cc] = (j < nk) ? x[(int64_t)cj[u] * K + cc] : T(0);
+        for (int cc = 0; cc < K; ++cc) xg[u][cc] = (j < nk) ? x[(int64_t)cj[u] * K + cc] : num<T>(0.f);
       }
       // x of the tile's rows: nre * K consecutive values
 #pragma unroll
       for (int u = 0; u <= kPer; ++u) {
         const int e = lane + 32 * u;
-        xrv[u] = (e < nre * K) ? x[(int64_t)r0 * K + e] : T(0);
+        xrv[u] = (e < nre * K) ? x[(int64_t)r0 * K + e] : num<T>(0.f);
       }
 #pragma unroll
       for (int u = 0; u < kPer; ++u) {
@@ -227,23 +230,23 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
     }
     int rl = lo;       // local row
     int k = dl - lo;   // local nonzero index
-    T xr = T(0);
+    T xr = num<T>(0.f);
     if (MODE == kLap && r0 + rl < g.n)
       xr = kStageX ? smx->xr[rl * K + c] : x[(int64_t)(r0 + rl) * K + c];
-    T acc = T(0);
+    T acc = num<T>(0.f);
     bool femit = false;
-    T fval = T(0);
+    T fval = num<T>(0.f);
     const int frl = rl;
     for (int it = dl; it < de; ++it) {
       const int rend = s_re[rl] - k0;
       if (k < rend) {
         const float w = g.val ? s_val[k] : 1.0f;
         if (MODE == kRowSum) {
-          acc += T(w);
+          acc += num<T>(w);
         } else {
           const T xj = kStageX ? smx->xj[k * K + c] : x[(int64_t)sm->col[k] * K + c];
           const T df = xr - xj;
-          const T tw = T(w) * df;
+          const T tw = mul_w(df, w);
           acc += tw;
           quad += tw * df;
         }
@@ -255,7 +258,7 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
         } else {
           out[(int64_t)(r0 + rl) * K + c] = acc;
         }
-        acc = T(0);
+        acc = num<T>(0.f);
         ++rl;
         if (MODE == kLap && r0 + rl < g.n)
           xr = kStageX ? smx->xr[rl * K + c] : x[(int64_t)(r0 + rl) * K + c];
@@ -272,13 +275,13 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
     T scan = cval;
 #pragma unroll
     for (int off = 1; off < G; off <<= 1) {
-      const T v = __shfl_up_sync(kFull, scan, off * K);
+      const T v = shfl_up_v(scan, off * K);
       const int32_t kr = __shfl_up_sync(kFull, crow, off * K);
       if (gw >= off && kr == crow) scan += v;
     }
-    const T prev = __shfl_up_sync(kFull, scan, K);
-    if (femit) out[(int64_t)(r0 + frl) * K + c] = fval + (gw > 0 ? prev : T(0));
-    carry = __shfl_sync(kFull, scan, (G - 1) * K + c);
+    const T prev = shfl_up_v(scan, K);
+    if (femit) out[(int64_t)(r0 + frl) * K + c] = fval + (gw > 0 ? prev : num<T>(0.f));
+    carry = shfl_v(scan, (G - 1) * K + c);
     carry_row = __shfl_sync(kFull, crow, (G - 1) * K + c);
   }
   if (lane == 0) wc_row[wg] = carry_row;
@@ -321,7 +324,22 @@ struct SellGraph {
 
 template <typename T, int K>
 __device__ __forceinline__ void load_k(const T* __restrict__ p, T (&v)[K]) {
-  if constexpr (K * sizeof(T) == 16 && sizeof(T) == 4) {
+  if constexpr (std::is_same<T, df64>::value) {
+    if constexpr (K % 2 == 0) {
+#pragma unroll
+      for (int cc = 0; cc < K; cc += 2) {
+        const float4 q = reinterpret_cast<const float4*>(p)[cc / 2];
+        v[cc] = df_make(q.x, q.y);
+        v[cc + 1] = df_make(q.z, q.w);
+      }
+    } else {
+#pragma unroll
+      for (int cc = 0; cc < K; ++cc) {
+        const float2 q = reinterpret_cast<const float2*>(p)[cc];
+        v[cc] = df_make(q.x, q.y);
+      }
+    }
+  } else if constexpr (K * sizeof(T) == 16 && sizeof(T) == 4) {
     const float4 q = *reinterpret_cast<const float4*>(p);
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
   } else if constexpr (K * sizeof(T) == 16 && sizeof(T) == 8) {
@@ -367,7 +385,7 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
       T xr[K], acc[K];
       load_k<T, K>(x + (int64_t)r * K, xr);
 #pragma unroll
-      for (int cc = 0; cc < K; ++cc) acc[cc] = T(0);
+      for (int cc = 0; cc < K; ++cc) acc[cc] = num<T>(0.f);
       // batches of kB entries per lane: all index loads, then all gathers
       for (int32_t p0 = b; p0 < e; p0 += 32 * kB) {
         int32_t j[kB];
@@ -386,7 +404,7 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
 #pragma unroll
           for (int cc = 0; cc < K; ++cc) {
             const T df = xr[cc] - xj[q][cc];
-            const T tw = T(w[q]) * df;
+            const T tw = mul_w(df, w[q]);
             acc[cc] += tw;
             quad[cc] += tw * df;
           }
@@ -395,7 +413,7 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
 #pragma unroll
       for (int cc = 0; cc < K; ++cc) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc[cc] += __shfl_xor_sync(kFull, acc[cc], off);
+        for (int off = 16; off > 0; off >>= 1) acc[cc] += shfl_xor_v(acc[cc], off);
       }
       T mine = acc[0];
 #pragma unroll
@@ -418,15 +436,15 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
           __threadfence();
           T tot[K];
 #pragma unroll
-          for (int cc = 0; cc < K; ++cc) tot[cc] = T(0);
+          for (int cc = 0; cc < K; ++cc) tot[cc] = num<T>(0.f);
           for (int32_t q = f + lane; q < f + nch; q += 32) {
 #pragma unroll
-            for (int cc = 0; cc < K; ++cc) tot[cc] += __ldcg(&part[(int64_t)q * K + cc]);
+            for (int cc = 0; cc < K; ++cc) tot[cc] += ldcg_v(&part[(int64_t)q * K + cc]);
           }
 #pragma unroll
           for (int cc = 0; cc < K; ++cc) {
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) tot[cc] += __shfl_xor_sync(kFull, tot[cc], off);
+            for (int off = 16; off > 0; off >>= 1) tot[cc] += shfl_xor_v(tot[cc], off);
           }
           T t = tot[0];
 #pragma unroll
@@ -445,7 +463,7 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
         T xr[K], acc[K];
         load_k<T, K>(x + row * K, xr);
 #pragma unroll
-        for (int cc = 0; cc < K; ++cc) acc[cc] = T(0);
+        for (int cc = 0; cc < K; ++cc) acc[cc] = num<T>(0.f);
         const int32_t* __restrict__ cp = g.sell_col + off + lane;
         const float* __restrict__ vp = g.sell_val ? g.sell_val + off + lane : nullptr;
         // batches of kB entries: all index loads, then all gathers
@@ -466,7 +484,7 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
 #pragma unroll
             for (int cc = 0; cc < K; ++cc) {
               const T df = xr[cc] - xj[q][cc];
-              const T tw = T(w[q]) * df;
+              const T tw = mul_w(df, w[q]);
               acc[cc] += tw;
               quad[cc] += tw * df;
             }
