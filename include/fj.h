@@ -190,6 +190,52 @@ fj_status fj_quantities(fj_ctx* ctx, const fj_graph* g, int32_t k,
                         fj_info* info);
 
 /* ---------------------------------------------------------------------
+ * Serving: continuous batching of solve requests (one worker thread per
+ * context, started by the first call below).  A request is queued on submit;
+ * it is admitted as soon as an in-flight slot is free and the device memory
+ * it needs fits the serving budget, and then runs on its own stream, side
+ * by side with the other admitted requests.  Finished requests release their
+ * memory and slot at once, so queued requests start while others still run.
+ * These calls may come from several threads.
+ */
+
+/* Sets the serving limits: at most max_inflight requests on the GPU at once
+ * (default 8; 0 keeps the current value), a device-memory budget for admitted
+ * requests (default half the free memory when serving starts; <= 0 keeps the
+ * current value) and a cap on the thread blocks of each request's solve
+ * (0: sized by the request alone; < 0 keeps the current value).
+ * Errors: FJ_ERR_ARG, FJ_ERR_CUDA. */
+fj_status fj_serve_config(fj_ctx* ctx, int32_t max_inflight,
+                          int64_t mem_budget_bytes,
+                          int32_t max_blocks_per_request);
+
+/* Queues the solve of k opinion vectors on a resident graph (which must stay
+ * alive until the request is collected).  s: HOST float64[n*k], column-major,
+ * copied before the call returns.  *ticket identifies the request for
+ * fj_poll.  Errors: FJ_ERR_ARG (1 <= k <= 1024), FJ_ERR_ADMIT (the request
+ * needs more device memory than the whole serving budget). */
+fj_status fj_submit(fj_ctx* ctx, const fj_graph* g, int32_t k,
+                    const double* s, const fj_opts* opts, uint64_t* ticket);
+
+/* Queues a request that brings its own graph: an edge list as for
+ * fj_graph_upload (HOST pointers, copied before the call returns).  The graph
+ * is built on the device when the request is admitted and freed when it
+ * finishes; a bad node id or weight is reported by fj_poll (FJ_ERR_GRAPH). */
+fj_status fj_submit_edges(fj_ctx* ctx, int64_t n, int64_t m,
+                          const int32_t* src, const int32_t* dst,
+                          const float* w, int32_t k, const double* s,
+                          const fj_opts* opts, uint64_t* ticket);
+
+/* Collects a request.  Waits up to timeout_us microseconds (0: do not wait,
+ * < 0: wait until done).  Returns FJ_PENDING while the request runs;
+ * otherwise the request's status (FJ_OK or a solve error) with out[0..k-1]
+ * (HOST) and *info filled (info->device_ms: milliseconds from admission to
+ * completion), and the ticket is consumed.  Errors: FJ_ERR_TICKET (unknown
+ * or already collected ticket). */
+fj_status fj_poll(fj_ctx* ctx, uint64_t ticket, int32_t timeout_us,
+                  fj_quant* out, fj_info* info);
+
+/* ---------------------------------------------------------------------
  * Allocation-free solve.  The paper has no counterpart: this entry point
  * serves callers that must not allocate device memory while solving - code
  * inside a latency-critical loop, where cudaMalloc/cudaFree could stall the

@@ -29,6 +29,19 @@ fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32
                           int max_blocks);
 
 namespace fj {
+struct Server;
+struct Request;
+Server* server_create(int device, int num_sms);
+void server_destroy(Server* S);
+fj_status server_config(Server* S, int32_t max_inflight, int64_t budget, int32_t max_blocks);
+fj_status server_submit(Server* S, Request* r, uint64_t* ticket);
+fj_status server_poll(Server* S, uint64_t ticket, int32_t timeout_us, fj_quant* out, fj_info* info);
+Request* request_new();
+void request_set_graph(Request* r, const fj_graph* g);
+void request_set_edges(Request* r, int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const float* w);
+void request_set_problem(Request* r, int32_t k, const double* s, int64_t n, const fj_opts& o);
+void request_delete(Request* r);
+constexpr int kServeMaxK = 1024;
 
 static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
@@ -104,6 +117,8 @@ struct fj_ctx {
   size_t z_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int max_blocks = 0;  // 0: all co-resident blocks
+  std::mutex server_mu;
+  fj::Server* server = nullptr;  // created by the first fj_submit / fj_serve_config
 };
 
 namespace {
@@ -202,6 +217,7 @@ fj_status fj_create(int device, fj_ctx** out) {
 
 fj_status fj_destroy(fj_ctx* c) {
   if (!c) return FJ_OK;
+  if (c->server) server_destroy(c->server);
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   if (c->ws) cudaFree(c->ws);
@@ -408,6 +424,100 @@ fj_status fj_quantities(fj_ctx* c, const fj_graph* g, int32_t k, const double* s
     return FJ_ERR_ARG;
   }
   return fj_solve_ex(c, g, k, s, nullptr, out, opts, info);
+}
+
+// ------------------------------------------------------------- serving
+
+static fj_status get_server(fj_ctx* c, fj::Server** out) {
+  std::lock_guard<std::mutex> lock(c->server_mu);
+  if (!c->server) {
+    c->server = server_create(c->device, c->num_sms);
+    if (!c->server) {
+      set_error("could not start the serving worker (streams / pinned buffers)");
+      return FJ_ERR_CUDA;
+    }
+  }
+  *out = c->server;
+  return FJ_OK;
+}
+
+static fj_status check_serve_args(int32_t k, const double* s, const fj_opts* opts, fj_opts* o) {
+  if (k < 1 || k > kServeMaxK || !s) {
+    set_error("fj_submit: need s non-NULL and 1 <= k <= %d (k=%d)", kServeMaxK, (int)k);
+    return FJ_ERR_ARG;
+  }
+  fj_default_opts(o);
+  if (opts) *o = *opts;
+  if (!(o->tol > 0.0) || !(o->inner_tol > 0.0) || o->inner_tol >= 1.0 || o->max_iter < 1 || o->max_refine < 1 ||
+      o->precision < 0 || o->precision > 2) {
+    set_error("fj_submit: invalid options");
+    return FJ_ERR_ARG;
+  }
+  return FJ_OK;
+}
+
+fj_status fj_serve_config(fj_ctx* c, int32_t max_inflight, int64_t mem_budget_bytes,
+                          int32_t max_blocks_per_request) {
+  if (!c || max_inflight < 0 || max_inflight > 256) {
+    set_error("fj_serve_config: bad argument");
+    return FJ_ERR_ARG;
+  }
+  fj::Server* S = nullptr;
+  fj_status rc = get_server(c, &S);
+  if (rc != FJ_OK) return rc;
+  return server_config(S, max_inflight, mem_budget_bytes, max_blocks_per_request);
+}
+
+fj_status fj_submit(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, const fj_opts* opts,
+                    uint64_t* ticket) {
+  if (!c || !g || !ticket) {
+    set_error("fj_submit: ctx, graph and ticket must be non-NULL");
+    return FJ_ERR_ARG;
+  }
+  if (g->device != c->device) {
+    set_error("fj_submit: graph belongs to device %d, context to %d", g->device, c->device);
+    return FJ_ERR_ARG;
+  }
+  fj_opts o;
+  fj_status rc = check_serve_args(k, s, opts, &o);
+  if (rc != FJ_OK) return rc;
+  fj::Server* S = nullptr;
+  rc = get_server(c, &S);
+  if (rc != FJ_OK) return rc;
+  fj::Request* r = request_new();
+  request_set_graph(r, g);
+  request_set_problem(r, k, s, g->n, o);
+  return server_submit(S, r, ticket);
+}
+
+fj_status fj_submit_edges(fj_ctx* c, int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                          const float* w, int32_t k, const double* s, const fj_opts* opts, uint64_t* ticket) {
+  if (!c || !ticket || n < 1 || n > (int64_t)INT32_MAX - 1 || m < 0 || 2 * m > (int64_t)INT32_MAX - 64 ||
+      (m > 0 && (!src || !dst))) {
+    set_error("fj_submit_edges: bad argument (n=%lld, m=%lld)", (long long)n, (long long)m);
+    return FJ_ERR_ARG;
+  }
+  fj_opts o;
+  fj_status rc = check_serve_args(k, s, opts, &o);
+  if (rc != FJ_OK) return rc;
+  fj::Server* S = nullptr;
+  rc = get_server(c, &S);
+  if (rc != FJ_OK) return rc;
+  fj::Request* r = request_new();
+  request_set_edges(r, n, m, src, dst, w);
+  request_set_problem(r, k, s, n, o);
+  return server_submit(S, r, ticket);
+}
+
+fj_status fj_poll(fj_ctx* c, uint64_t ticket, int32_t timeout_us, fj_quant* out, fj_info* info) {
+  if (!c) {
+    set_error("fj_poll: ctx is NULL");
+    return FJ_ERR_ARG;
+  }
+  fj::Server* S = nullptr;
+  fj_status rc = get_server(c, &S);
+  if (rc != FJ_OK) return rc;
+  return server_poll(S, ticket, timeout_us, out, info);
 }
 
 }  // extern "C"

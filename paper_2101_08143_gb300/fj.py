@@ -83,6 +83,13 @@ _SIGNATURES = {
                                   ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
     "fj_quantities": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P,
                                        ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
+    "fj_serve_config": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]),
+    "fj_submit": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, ctypes.POINTER(Opts),
+                                   ctypes.POINTER(ctypes.c_uint64)]),
+    "fj_submit_edges": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
+                                         ctypes.c_int32, _P, ctypes.POINTER(Opts),
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "fj_poll": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.c_int32, _P, ctypes.POINTER(Info)]),
 }
 
 _lib = None
@@ -276,6 +283,74 @@ class Context:
     def quantities(self, graph: Graph, s, opts: Opts | None = None):
         _, q, info = self.solve(graph, s, want_z=False, want_quant=True, opts=opts)
         return q, info
+
+
+class Ticket:
+    """A submitted request: its id and the number of opinion vectors."""
+
+    def __init__(self, tid: int, k: int):
+        self.id = tid
+        self.k = k
+
+
+def _host_s(s, n):
+    s = np.asarray(s, dtype=np.float64)
+    s2 = np.asfortranarray(s.reshape(n, -1))
+    return s2, s2.shape[1]
+
+
+def _serve_opts(opts):
+    o = Opts()
+    load().fj_default_opts(ctypes.byref(o))
+    if opts is not None:
+        o = Opts(opts.tol, opts.inner_tol, opts.precision, opts.max_iter, opts.max_refine, 0)
+    return o
+
+
+def serve_config(ctx: "Context", max_inflight=0, mem_budget_bytes=0, max_blocks_per_request=-1):
+    _check(load().fj_serve_config(ctx.handle, int(max_inflight), int(mem_budget_bytes),
+                                  int(max_blocks_per_request)), "fj_serve_config")
+
+
+def submit(ctx: "Context", graph: "Graph", s, opts: Opts | None = None) -> Ticket:
+    """Queue a solve on a resident graph; s is host float64 (n,) or (n, k)."""
+    n = graph.stats()["n"]
+    s2, k = _host_s(s, n)
+    t = ctypes.c_uint64()
+    o = _serve_opts(opts)
+    _check(load().fj_submit(ctx.handle, graph.handle, k, _P(s2.ctypes.data), ctypes.byref(o),
+                            ctypes.byref(t)), "fj_submit")
+    return Ticket(t.value, k)
+
+
+def submit_edges(ctx: "Context", n, src, dst, w, s, opts: Opts | None = None) -> Ticket:
+    """Queue a request that carries its own edge list (host arrays)."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+    s2, k = _host_s(s, n)
+    t = ctypes.c_uint64()
+    o = _serve_opts(opts)
+    _check(load().fj_submit_edges(ctx.handle, int(n), int(src.shape[0]), _P(src.ctypes.data),
+                                  _P(dst.ctypes.data), _P(None if w is None else w.ctypes.data), k,
+                                  _P(s2.ctypes.data), ctypes.byref(o), ctypes.byref(t)),
+           "fj_submit_edges")
+    return Ticket(t.value, k)
+
+
+def poll(ctx: "Context", ticket: Ticket, timeout_us: int = -1):
+    """Returns (rc, quantities or None, info dict).  rc == FJ_PENDING while
+    the request runs."""
+    quant = (Quant * ticket.k)()
+    info = Info()
+    rc = load().fj_poll(ctx.handle, ticket.id, int(timeout_us), ctypes.cast(quant, _P),
+                        ctypes.byref(info))
+    if rc == FJ_PENDING:
+        return rc, None, None
+    qs = [{name: getattr(quant[j], name) for name in QUANTITY_NAMES} for j in range(ticket.k)]
+    d = info.as_dict()
+    d["rc"] = rc
+    return rc, qs, d
 
 
 def version() -> str:

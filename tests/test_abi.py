@@ -51,3 +51,12 @@ def test_built_for_sm_103a():
     from paper_2101_08143_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
     assert os.path.exists(build.LIB)
+
+
+def test_serving_arguments_rejected_without_a_device():
+    import ctypes as C
+    lib = fj.load()
+    t = C.c_uint64()
+    assert lib.fj_submit(None, None, 1, None, None, C.byref(t)) == fj.FJ_ERR_ARG
+    assert lib.fj_poll(None, 1, 0, None, None) == fj.FJ_ERR_ARG
+    assert lib.fj_serve_config(None, 1, 0, 0) == fj.FJ_ERR_ARG
