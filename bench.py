@@ -161,6 +161,104 @@ def aggregate(local_ms, units_per_rank, dist=None, device=None):
     return world * units_per_rank / (t / 1000.0), t
 
 
+def precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush, reps=5):
+    """Solve-only throughput on the resident bench graph, all modes to the
+    same relative residual: plain float64 PCG (one opinion vector), mixed
+    precision (one vector) and mixed precision with 32 vectors per call."""
+    out = {}
+    rng = np.random.default_rng(17)
+    dev = src_d.device
+    s32 = torch.from_numpy(rng.random((32, g.n))).to(dev)
+    s1 = s32[:1].contiguous()
+    with torch.cuda.stream(stream):
+        gr = ctx.upload(g.n, src_d, dst_d, w_d)
+        for name, prec, sv in (("fp64_k1", fj.PREC_FP64, s1), ("mixed_k1", fj.PREC_MIXED, s1),
+                               ("mixed_k32", fj.PREC_MIXED, s32)):
+            o = fj.default_opts(tol=TOL, precision=prec)
+            ctx.solve(gr, sv, opts=o, want_z=False)
+            ms, res = [], 0.0
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                _, _, info = ctx.solve(gr, sv, opts=o, want_z=False)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+                res = max(res, info["rel_residual"])
+            k = sv.shape[0]
+            out[name] = {"column_solves_per_s": k * 1000.0 / float(np.median(ms)),
+                         "ms_per_call": float(np.median(ms)), "k": k, "rel_residual": res,
+                         "iterations": info["iterations"]}
+        gr.free()
+    return out
+
+
+def serving_run(ctx, fj, n_requests=240, seed=4, rate_frac=0.5):
+    """A Poisson stream of requests that bring their own graph (Erdos-Renyi or
+    Chung-Lu, n log-uniform in [10^3, 10^5], average degree U[4, 20],
+    weights U(0,1], 1-16 opinion vectors) through fj_submit_edges / fj_poll.
+    First the saturation throughput (all requests at once), then an open
+    loop at rate_frac of it; latency = submit to completion."""
+    import threading
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(24):
+        n = int(10 ** rng.uniform(3, 5))
+        m = int(n * rng.uniform(4, 20) / 2)
+        if rng.random() < 0.5:
+            gg = synth.erdos_renyi(n, m, seed=seed * 100 + i, weighted=True)
+        else:
+            gg = synth.chung_lu(n, m, rng.uniform(2.1, 2.5), seed=seed * 100 + i, weighted=True)
+        pool.append(gg)
+    reqs = []
+    for r in range(n_requests):
+        gg = pool[int(rng.integers(0, len(pool)))]
+        k = int(rng.integers(1, 17))
+        reqs.append((gg, rng.random((gg.n, k))))
+
+    def run(gaps):
+        t_sub, t_done = [0.0] * len(reqs), [0.0] * len(reqs)
+        tickets = [None] * len(reqs)
+        ready = threading.Semaphore(0)
+
+        def poller():
+            for i in range(len(reqs)):
+                ready.acquire()
+                rc, _, _ = fj.poll(ctx, tickets[i], -1)
+                t_done[i] = time.perf_counter()
+                assert rc == fj.FJ_OK
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        for i, (gg, sv) in enumerate(reqs):
+            if gaps is not None:
+                target = t0 + gaps[i]
+                while time.perf_counter() < target:
+                    time.sleep(max(0.0, min(0.001, target - time.perf_counter())))
+            t_sub[i] = time.perf_counter()
+            tickets[i] = fj.submit_edges(ctx, gg.n, gg.src, gg.dst, gg.w, sv)
+            ready.release()
+        th.join()
+        lat = 1000.0 * (np.array(t_done) - np.array(t_sub))
+        span = max(t_done) - t0
+        cols = sum(sv.shape[1] for _, sv in reqs)
+        return lat, span, cols
+
+    run(None)  # warm-up
+    lat, span, cols = run(None)
+    sat = len(reqs) / span
+    arrivals = np.cumsum(rng.exponential(1.0 / (rate_frac * sat), len(reqs)))
+    lat2, span2, _ = run(arrivals)
+    return {"requests": len(reqs), "graph_pool": len(pool),
+            "saturation_requests_per_s": sat, "saturation_column_solves_per_s": cols / span,
+            "open_loop_rate_per_s": rate_frac * sat,
+            "latency_ms": {"p50": float(np.percentile(lat2, 50)), "p99": float(np.percentile(lat2, 99))},
+            "saturated_latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                     "p99": float(np.percentile(lat, 99))}}
+
+
 def run_cpu_baseline(g, s, n_solves, tol=TOL):
     import oracle.fj_oracle as fo
     t0 = time.perf_counter()
@@ -212,6 +310,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--cpu-solves", type=int, default=3, help="oracle solves in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -337,6 +436,9 @@ def main():
     h2d = g.m * 4 * (3 if weighted else 2) + g.n * k * 8
     d2h = g.n * k * 8 + k * 5 * 8
 
+    compare = precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush)
+    serving = serving_run(ctx, fj) if not args.no_serving else None
+
     line = None
     if rank == 0:
         line = {
@@ -365,6 +467,8 @@ def main():
             "wall_s_timed": wall,
             "clocks": clk,
             "quantities": q[0],
+            "precision_compare": compare,
+            "serving": serving,
         }
     ctx.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
