@@ -60,6 +60,8 @@ struct SolveParams {
   VI* hub_part;         // [n_chunks][K] chunk sums of multi-chunk rows
   df64* hub_part64;
   int* hub_cnt;         // [n_long] finished chunks per long row
+  double* quad_u;       // [n_units][K] edge sums per work unit (K >= 8)
+  unsigned long long* unit_counter;  // next work unit of the wide walks
   const float* dinv;
   // problem (column c of this launch: s + c*ld)
   const double* s;
@@ -132,6 +134,7 @@ template <int K, int NS>
 __device__ __forceinline__ void block_store(const double (&v)[NS], const int (&slots)[NS],
                                             double* part, double* red /*[NS][kWarps][K]*/) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();  // red aliases the walks' shared staging
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
     double x = v[j];
@@ -169,6 +172,48 @@ __device__ __forceinline__ void grid_reduce(const int (&slots)[NS], const double
 
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 
+// SpMM walk for K >= 8: the warps of the whole grid take work units one at a
+// time from one counter, in unit order (hub chunks first, then slices by
+// falling degree), so the walk ends with at most one unit per warp in flight.
+// The counter only grows: a walk starting at value `base` hands out units
+// base + [0, n_units) and ends at base + n_units + (number of warps), each
+// warp having drawn exactly one value past the end.  Each unit's edge sum
+// sum w (x_r - x_j)^2 is stored per unit and column (quad_u); unit_sum adds
+// them up after the walk's barrier in a fixed partition, so the result does
+// not depend on which warp took which unit.
+template <typename T, int K>
+__device__ __forceinline__ void wide_walk(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
+                                          T* __restrict__ part, int* __restrict__ cnt,
+                                          unsigned long long* counter, unsigned long long base,
+                                          double* __restrict__ quad_u, T* __restrict__ sxr) {
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    unsigned long long k = 0;
+    if (lane == 0) k = atomicAdd(counter, 1ull) - base;
+    const int64_t u = (int64_t)__shfl_sync(kFull, k, 0);
+    if (u >= g.n_units) break;
+    T q = num<T>(0.f);
+    wide_unit<T, K>(g, x, out, part, cnt, u, q, sxr);
+    double qd = to_double(q);
+#pragma unroll
+    for (int off = K; off < 32; off <<= 1) qd += __shfl_xor_sync(kFull, qd, off);
+    if (lane < K) quad_u[u * K + lane] = qd;
+  }
+}
+
+// This thread's share of the block's sum of quad_u over units [ub0, ub1):
+// column c = tid % K, group tid / K takes a fixed contiguous sub-range.
+template <int K>
+__device__ __forceinline__ double unit_sum(const double* __restrict__ quad_u, int64_t ub0, int64_t ub1) {
+  constexpr int G = kThreads / K;
+  const int c = threadIdx.x % K, gi = threadIdx.x / K;
+  const int64_t len = ub1 - ub0;
+  const int64_t a = ub0 + len * gi / G, b = ub0 + len * (gi + 1) / G;
+  double s = 0.0;
+  for (int64_t u = a; u < b; ++u) s += __ldcg(&quad_u[u * K + c]);
+  return s;
+}
+
 // A lane holding partial sums for all K columns hands them to block_store,
 // which sums lanes of equal column lane % K: lane c < K gets the warp total of
 // column c, every other lane 0.
@@ -193,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   constexpr size_t kTileBytes = tile_smem_bytes<VI, K>() > tile_smem_bytes<double, K>()
                                     ? tile_smem_bytes<VI, K>()
                                     : tile_smem_bytes<double, K>();
-  __shared__ double red[7 * kWarps * K];
+  double* red = reinterpret_cast<double*>(smem_raw);  // [7][kWarps][K], aliases the staging
   __shared__ double res[NSLOT * K];
   __shared__ double alpha[K], beta[K], gam_prev[K], alpha_prev[K], rr_goal[K], mu[K], bb[K];
   __shared__ int active[K], first[K], done[K], inner_ok[K];
@@ -206,22 +251,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   const int64_t gstride = (int64_t)gridDim.x * kThreads;
   const int c = threadIdx.x % K;
   const int64_t wg = (int64_t)blockIdx.x * kWarps + warp;
-  void* my_tsm = smem_raw + warp * kTileBytes;
+  // per-warp staging of the wide walks' row values
+  VI* my_sxr = reinterpret_cast<VI*>(smem_raw + warp * kGatherBytesPerWarp);
+  df64* my_sxr64 = reinterpret_cast<df64*>(my_sxr);
   int* status = P.status;
   const bool fp32_mode = P.mode == kModeFP32;
   unsigned epoch = 0;  // barriers passed (used by thread 0)
-  constexpr bool kSell = K <= 4;
-  // this warp's share of the sliced-ELL work units
+  // every K walks the same work units (sliced ELL for K <= 4, lanes as
+  // columns for K >= 8), so all row sums are complete after a walk
+  constexpr bool kSell = true;
+  constexpr bool kWide = K >= 8;
+
+  // K <= 4: this warp's share of the work units, split by cost;
+  // K >= 8: the units whose edge sums this block adds up (even split)
   int64_t u0 = 0, u1 = 0;
-  if (kSell) {
+  unsigned long long unit_base = 0;  // unit counter at the start of the next wide walk
+  if constexpr (kWide) {
+    u0 = P.sg.n_units * (int64_t)blockIdx.x / gridDim.x;
+    u1 = P.sg.n_units * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  } else {
     const int lane = threadIdx.x & 31;
     const int64_t W = (int64_t)gridDim.x * kWarps;
     int64_t v = 0;
     if (lane < 2) v = sell_unit_start(P.sg, wg + lane, W);
     u0 = __shfl_sync(kFull, v, 0);
     u1 = __shfl_sync(kFull, v, 1);
-    for (int64_t i = gtid; i < P.sg.n_long; i += gstride) P.hub_cnt[i] = 0;
   }
+  for (int64_t i = gtid; i < P.sg.n_long; i += gstride) P.hub_cnt[i] = 0;
+  const unsigned long long unit_step = (unsigned long long)P.sg.n_units + (unsigned long long)gridDim.x * kWarps;
 
   // ---------------------------------------------------------------- setup
   {
@@ -269,10 +326,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         } else {
           sb = P.sbar[idx];
           qv = P.q[idx];
-          if (kSell)
-            lq = i < P.sg.n_nz ? P.t64[idx] : z0;
-          else
-            lq = row_total<df64, K>(i, P.t64[idx], P.g.row_ptr, P.wc_val64, P.g.items_per_warp, c);
+          lq = i < P.sg.n_nz ? P.t64[idx] : z0;
         }
         const df64 r64 = df_sub(df_sub(sb, qv), lq);
         a_rr64 += df_mul(r64, r64);
@@ -372,13 +426,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       {
         double qv;
         if constexpr (kSell) {
-          VI quad[K];
+          if constexpr (kWide) {
+            wide_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.hub_cnt, P.unit_counter, unit_base, P.quad_u, my_sxr);
+            unit_base += unit_step;
+            if (!grid_sync(P.bar, status, epoch)) return;
+            qv = unit_sum<K>(P.quad_u, u0, u1);
+          } else {
+            VI quad[K];
 #pragma unroll
-          for (int cc = 0; cc < K; ++cc) quad[cc] = VI(0);
-          sell_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.hub_cnt, u0, u1, quad);
-          qv = lane_share<VI, K>(quad);
-        } else {
-          qv = (double)walk_tiles<VI, K, kLap>(P.g, P.u, P.t, P.wc_row, P.wc_val, wg, my_tsm);
+            for (int cc = 0; cc < K; ++cc) quad[cc] = VI(0);
+            sell_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.hub_cnt, u0, u1, quad);
+            qv = lane_share<VI, K>(quad);
+          }
         }
         const double v[1] = {qv};
         const int sl[1] = {S_EQ};
@@ -443,8 +502,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
             if (idx < NK) {
               const int64_t i = idx / K;
               uv[e] = vu[idx];
-              tv[e] = kSell ? (i < P.sg.n_nz ? vt[idx] : VI(0))
-                            : row_total<VI, K>(i, vt[idx], P.g.row_ptr, P.wc_val, P.g.items_per_warp, c);
+              tv[e] = i < P.sg.n_nz ? vt[idx] : VI(0);
               pv[e] = fst ? VI(0) : vp[idx];
               dv[e] = fst ? VI(0) : vd[idx];
               xv[e] = vx[idx];
@@ -521,13 +579,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
     {
       double quad;
       if constexpr (kSell) {
-        df64 qd[K];
+        if constexpr (kWide) {
+          wide_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, P.hub_cnt, P.unit_counter, unit_base, P.quad_u,
+                             my_sxr64);
+          unit_base += unit_step;
+          if (!grid_sync(P.bar, status, epoch)) return;
+          quad = unit_sum<K>(P.quad_u, u0, u1);
+        } else {
+          df64 qd[K];
 #pragma unroll
-        for (int cc = 0; cc < K; ++cc) qd[cc] = df_from_float(0.0f);
-        sell_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, P.hub_cnt, u0, u1, qd);
-        quad = lane_share<df64, K>(qd);
-      } else {
-        quad = df_to_double(walk_tiles<df64, K, kLap>(P.g, P.q, P.t64, P.wc_row, P.wc_val64, wg, my_tsm));
+          for (int cc = 0; cc < K; ++cc) qd[cc] = df_from_float(0.0f);
+          sell_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, P.hub_cnt, u0, u1, qd);
+          quad = lane_share<df64, K>(qd);
+        }
       }
       const double v[1] = {quad};
       const int sl[1] = {S_D};
@@ -562,7 +626,9 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
                             int64_t ld, double* z, double* quant, double* resid, int* status,
                             char* ws, size_t ws_bytes, const fj_opts& o, int mode, int max_blocks) {
   auto kern = k_solve<VI, K>;
-  const size_t dyn = (K <= 4) ? 0 : kWarps * std::max(tile_smem_bytes<VI, K>(), tile_smem_bytes<double, K>());
+  const size_t red_bytes = (size_t)7 * kWarps * K * sizeof(double);
+  const size_t stage = (K <= 4) ? 0 : (size_t)kWarps * kGatherBytesPerWarp;
+  const size_t dyn = std::max(red_bytes, stage);
   FJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int per_sm = 0;
   FJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, dyn));
@@ -621,7 +687,9 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.hub_part = (VI*)take(std::max<int64_t>(g->n_chunks, 1) * K * sizeof(VI));
   P.hub_part64 = (df64*)take(std::max<int64_t>(g->n_chunks, 1) * K * 8);
   P.hub_cnt = (int*)take(std::max<int64_t>(g->n_long, 1) * 4);
-  P.bar = (Barrier*)take(sizeof(Barrier));
+  P.quad_u = (double*)take(std::max<int64_t>(g->n_units, 1) * K * 8);
+  P.bar = (Barrier*)take(64);  // the barrier, then the unit counter
+  P.unit_counter = (unsigned long long*)((char*)P.bar + 32);
   if (off > ws_bytes) {
     set_error("internal: workspace too small (%zu > %zu)", off, ws_bytes);
     return FJ_ERR_OOM;
@@ -631,7 +699,7 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.max_iter = o.max_iter;
   P.max_refine = o.max_refine;
   P.mode = mode;
-  FJ_CUDA(cudaMemsetAsync(P.bar, 0, sizeof(Barrier), st));
+  FJ_CUDA(cudaMemsetAsync(P.bar, 0, 64, st));
   void* args[] = {&P};
   FJ_CUDA(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(kThreads), args, dyn, st));
   count_launches(1);
@@ -660,7 +728,8 @@ size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int n
   add(std::max<int64_t>(g->n_chunks, 1) * K * inner_bytes);
   add(std::max<int64_t>(g->n_chunks, 1) * K * 8);
   add(std::max<int64_t>(g->n_long, 1) * 4);
-  add(sizeof(Barrier));
+  add(std::max<int64_t>(g->n_units, 1) * K * 8);
+  add(64);
   return b;
 }
 

@@ -96,6 +96,28 @@ inline void set_tiles_per_warp(WalkGraph& g, int64_t tpw) {
 
 enum WalkMode { kRowSum = 0, kLap = 1 };
 
+// Asynchronous 4/8-byte copies global -> shared (no registers held while
+// in flight); cp.async.wait_all makes the executing thread's copies visible.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Wide walks (K >= 8) prefetch the x rows of the next kPrefetch<T> nonzeros
+// of each walker into this much shared memory per warp.
+constexpr int kGatherBytesPerWarp = 4096;
+template <typename T>
+struct Prefetch {
+  static constexpr int value = kGatherBytesPerWarp / (32 * (int)sizeof(T));  // nonzeros per walker
+};
+
 // Walks tiles [wg*tpw, (wg+1)*tpw) of the merge path.
 //   kRowSum: out[r] = sum of row r's weights (K must be 1, x unused)
 //   kLap:    out[r*K+c] = sum_j w_rj (x[r*K+c] - x[j*K+c]); returns this
@@ -105,8 +127,12 @@ enum WalkMode { kRowSum = 0, kLap = 1 };
 template <typename T, int K, int MODE>
 __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict__ x,
                                         T* __restrict__ out, int32_t* __restrict__ wc_row,
-                                        T* __restrict__ wc_val, int64_t wg, void* smem) {
+                                        T* __restrict__ wc_val, int64_t wg, void* smem,
+                                        T* __restrict__ gbuf = nullptr) {
   constexpr bool kStageX = (MODE == kLap) && StagesX<T, K>::value;
+  // wide walks: x rows of upcoming nonzeros prefetched into gbuf (per walker)
+  constexpr bool kPre = (MODE == kLap) && !kStageX && K >= 8;
+  constexpr int PD = Prefetch<T>::value;
   TileSmem* sm = reinterpret_cast<TileSmem*>(smem);
   TileSmemX<T, K>* smx = reinterpret_cast<TileSmemX<T, K>*>(smem);
   int32_t* s_re = kStageX ? smx->re : sm->re;
@@ -231,12 +257,32 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
     int rl = lo;       // local row
     int k = dl - lo;   // local nonzero index
     T xr = num<T>(0.f);
+    T xr_nx = num<T>(0.f);  // wide walks: x of the next row, loaded one row ahead
     if (MODE == kLap && r0 + rl < g.n)
       xr = kStageX ? smx->xr[rl * K + c] : x[(int64_t)(r0 + rl) * K + c];
+    if (kPre && r0 + rl + 1 < g.n) xr_nx = x[(int64_t)(r0 + rl + 1) * K + c];
     T acc = num<T>(0.f);
     bool femit = false;
     T fval = num<T>(0.f);
     const int frl = rl;
+    // Two halves of PD/2 nonzeros: one being read, the next one in flight.
+    constexpr int HB = PD / 2;
+    int cbase = -1;  // local index of the first nonzero of the half being read
+    int cur = 0;     // which half is being read
+    T* wbuf = gbuf + gw * PD * K;
+    auto issue_half = [&](int base, int half) {
+#pragma unroll 4
+      for (int i = 0; i < HB; ++i) {
+        if (base + i < nk) {
+          const T* src = x + (int64_t)sm->col[base + i] * K + c;
+          if constexpr (sizeof(T) == 4)
+            cp_async4(&wbuf[(half * HB + i) * K + c], src);
+          else
+            cp_async8(&wbuf[(half * HB + i) * K + c], src);
+        }
+      }
+      cp_async_commit_group();
+    };
     for (int it = dl; it < de; ++it) {
       const int rend = s_re[rl] - k0;
       if (k < rend) {
@@ -244,7 +290,22 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
         if (MODE == kRowSum) {
           acc += num<T>(w);
         } else {
-          const T xj = kStageX ? smx->xj[k * K + c] : x[(int64_t)sm->col[k] * K + c];
+          if (kPre) {  // walker-uniform; each lane reads and copies only its own column
+            if (cbase < 0) {
+              cbase = k;
+              cur = 0;
+              issue_half(k, 0);
+              issue_half(k + HB, 1);
+              cp_async_wait_one();
+            } else if (k >= cbase + HB) {
+              cbase += HB;
+              cur ^= 1;
+              issue_half(cbase + HB, cur ^ 1);
+              cp_async_wait_one();
+            }
+          }
+          const T xj = kStageX ? smx->xj[k * K + c]
+                               : (kPre ? wbuf[(cur * HB + (k - cbase)) * K + c] : x[(int64_t)sm->col[k] * K + c]);
           const T df = xr - xj;
           const T tw = mul_w(df, w);
           acc += tw;
@@ -260,10 +321,15 @@ __device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict_
         }
         acc = num<T>(0.f);
         ++rl;
-        if (MODE == kLap && r0 + rl < g.n)
+        if (kPre) {
+          xr = xr_nx;
+          if (r0 + rl + 1 < g.n) xr_nx = x[(int64_t)(r0 + rl + 1) * K + c];
+        } else if (MODE == kLap && r0 + rl < g.n) {
           xr = kStageX ? smx->xr[rl * K + c] : x[(int64_t)(r0 + rl) * K + c];
+        }
       }
     }
+    if (kPre && cbase >= 0) cp_async_wait_all();  // the buffer is reused by the next tile
     int32_t crow = r0 + rl;
     T cval = acc;
     if (gw == 0) {
@@ -492,6 +558,154 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
         }
 #pragma unroll
         for (int cc = 0; cc < K; ++cc) out[row * K + cc] = acc[cc];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------- wide (K >= 8)
+//
+// 8, 16 or 32 right-hand sides: lanes hold columns.  A warp is SUB = 32/K
+// sub-groups of K lanes; every gathered row x_j is one K-wide coalesced load.
+// Work units are the same as for narrow K (long-row chunks, 32-row slices):
+//   chunk: the sub-groups stride over the chunk's entries, kWB entries per
+//          sub-group in flight, then an xor tree across sub-groups; chunks
+//          of one row are finished as in chunk_walk;
+//   slice: sub-group sg owns the RB = 32/SUB consecutive rows
+//          [rs + sg*RB, rs + (sg+1)*RB); their entries are one contiguous run
+//          of the CSR, summed in batches of kWB entries that run across row
+//          ends.  The rows' end offsets sit in lane registers (one shuffle per
+//          row end) and their x values are staged in shared memory first.
+constexpr int kWB = 8;
+
+template <typename T, int K>
+__device__ __forceinline__ void wide_unit(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
+                                          T* __restrict__ part, int* __restrict__ cnt, int64_t u, T& quad,
+                                          T* __restrict__ sxr) {
+  constexpr int SUB = 32 / K;
+  constexpr int RB = 32 / SUB;  // rows per sub-group in a slice
+  const int lane = threadIdx.x & 31;
+  const int sg = lane / K, c = lane % K;
+  const unsigned smask = (K == 32) ? kFull : (((1u << K) - 1u) << (sg * K));
+  if (u < g.n_chunks) {
+    const int32_t r = g.chunk_row[u];
+    const int32_t b = g.chunk_begin[u], e = g.chunk_end[u];
+    const T xr = x[(int64_t)r * K + c];
+    T acc = num<T>(0.f);
+    for (int32_t p0 = b + sg; p0 < e; p0 += SUB * kWB) {
+      int32_t j[kWB];
+      float w[kWB];
+#pragma unroll
+      for (int t = 0; t < kWB; ++t) {
+        const int32_t p = p0 + t * SUB;
+        const bool in = p < e;
+        j[t] = in ? g.col[p] : r;
+        w[t] = in ? (g.val ? g.val[p] : 1.0f) : 0.0f;
+      }
+      T xj[kWB];
+#pragma unroll
+      for (int t = 0; t < kWB; ++t) xj[t] = x[(int64_t)j[t] * K + c];
+#pragma unroll
+      for (int t = 0; t < kWB; ++t) {
+        const T df = xr - xj[t];
+        const T tw = mul_w(df, w[t]);
+        acc += tw;
+        quad += tw * df;
+      }
+    }
+#pragma unroll
+    for (int off = K; off < 32; off <<= 1) acc += shfl_xor_v(acc, off);
+    const int32_t f = g.long_first[r];
+    const int32_t nch = g.long_first[r + 1] - f;
+    if (nch == 1) {
+      if (sg == 0) out[(int64_t)r * K + c] = acc;
+      return;
+    }
+    if (sg == 0) {
+      part[u * K + c] = acc;
+      __threadfence();
+    }
+    __syncwarp();
+    int done = 0;
+    if (lane == 0) done = atomicAdd(&cnt[r], 1) == nch - 1;
+    done = __shfl_sync(kFull, done, 0);
+    if (!done) return;
+    __threadfence();
+    T tot = num<T>(0.f);
+    for (int32_t q = f + sg; q < f + nch; q += SUB) tot += ldcg_v(&part[(int64_t)q * K + c]);
+#pragma unroll
+    for (int off = K; off < 32; off <<= 1) tot += shfl_xor_v(tot, off);
+    if (sg == 0) out[(int64_t)r * K + c] = tot;
+    if (lane == 0) cnt[r] = 0;
+    return;
+  }
+  // slice: rows [ra, rb) of this sub-group; row i of the slice is owned by
+  // sub-group i / RB, whose lanes are [i / RB * K, ...) = the lanes that
+  // hold the row ends of its rows (RB == K).
+  constexpr bool kStageXr = 32 * K * (int)sizeof(T) <= kGatherBytesPerWarp;
+  const int64_t s = u - g.n_chunks;
+  const int64_t rs = g.n_long + 32 * s;
+  const int64_t ra = rs + (int64_t)sg * RB;
+  int64_t rb = ra + RB;
+  if (rb > g.n_nz) rb = g.n_nz;
+  // lane l of the warp holds row_ptr[rs + l + 1], the end of row rs + l
+  const int64_t rr = rs + lane;
+  const int32_t rend_l = (rr < g.n_nz) ? g.row_ptr[rr + 1] : 0;
+  if (kStageXr) {  // x of the slice's 32 rows: row i at sxr[i*K + c]
+    __syncwarp();
+    for (int i = sg; i < 32; i += SUB) {
+      const int64_t row = rs + i;
+      sxr[i * K + c] = (row < g.n) ? x[row * K + c] : num<T>(0.f);
+    }
+    __syncwarp();
+  }
+  const int il = (int)((ra < rb ? ra : rs) - rs);
+  const int ie = (int)((ra < rb ? rb - 1 : rs) - rs);
+  int32_t cend = __shfl_sync(kFull, rend_l, il);
+  const int32_t pend = __shfl_sync(kFull, rend_l, ie);
+  if (ra >= rb) return;
+  int32_t p = g.row_ptr[ra];
+  int64_t cur = ra;  // current row
+  T xr = kStageXr ? sxr[(cur - rs) * K + c] : x[cur * K + c];
+  T acc = num<T>(0.f);
+  while (true) {
+    // rows without entries end at once
+    while (cur < rb && p >= cend) {
+      out[cur * K + c] = acc;
+      acc = num<T>(0.f);
+      ++cur;
+      if (cur < rb) {
+        cend = __shfl_sync(smask, rend_l, (int)(cur - rs));
+        xr = kStageXr ? sxr[(cur - rs) * K + c] : x[cur * K + c];
+      }
+    }
+    if (cur >= rb) break;
+    int32_t j[kWB];
+    float w[kWB];
+#pragma unroll
+    for (int t = 0; t < kWB; ++t) {
+      const bool in = p + t < pend;
+      j[t] = in ? g.col[p + t] : 0;
+      w[t] = in ? (g.val ? g.val[p + t] : 1.0f) : 0.0f;
+    }
+    T xj[kWB];
+#pragma unroll
+    for (int t = 0; t < kWB; ++t) xj[t] = x[(int64_t)j[t] * K + c];
+#pragma unroll
+    for (int t = 0; t < kWB; ++t) {
+      if (p < pend) {
+        while (p >= cend) {  // row end inside the batch
+          out[cur * K + c] = acc;
+          acc = num<T>(0.f);
+          ++cur;
+          cend = __shfl_sync(smask, rend_l, (int)(cur - rs));
+          xr = kStageXr ? sxr[(cur - rs) * K + c] : x[cur * K + c];
+        }
+        const T df = xr - xj[t];
+        const T tw = mul_w(df, w[t]);
+        acc += tw;
+        quad += tw * df;
+        ++p;
       }
     }
   }

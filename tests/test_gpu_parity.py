@@ -124,9 +124,30 @@ def test_launch_shapes_agree(ctx, blocks):
     np.testing.assert_allclose(z, zo[:, 0], atol=1e-8)
 
 
-def test_deterministic_bits(ctx):
+@pytest.mark.parametrize("blocks", [1, 3])
+def test_launch_shapes_agree_wide(ctx, blocks):
+    """A 16-column launch on grids of one and three blocks matches the oracle."""
+    g = synth.chung_lu(20_000, 80_000, 2.3, seed=8, weighted=True)
+    s = synth.opinions_uniform(g.n, 16, 4)
+    zo, qo = _oracle(g, s)
+    ctx.set_max_blocks(blocks)
+    try:
+        with ctx.upload_edges(g) as dg:
+            z, q, _ = ctx.solve(dg, s)
+    finally:
+        ctx.set_max_blocks(0)
+    for j in range(16):
+        _check_quantities(q[j], qo[j], s[:, j], 1e-6)
+    np.testing.assert_allclose(z, zo, atol=1e-8)
+
+
+@pytest.mark.parametrize("k", [2, 40])
+def test_deterministic_bits(ctx, k):
+    """Repeated solves, and solves on a re-uploaded graph, give the same bits;
+    k = 40 runs the 32- and 8-column launches, whose warps take work units
+    in whatever order they become free."""
     g = synth.chung_lu(30_000, 120_000, 2.2, seed=9, weighted=True)
-    s = synth.opinions_uniform(g.n, 2, 6)
+    s = synth.opinions_uniform(g.n, k, 6)
     with ctx.upload_edges(g) as dg:
         z1, q1, _ = ctx.solve(dg, s)
         z2, q2, _ = ctx.solve(dg, s)
