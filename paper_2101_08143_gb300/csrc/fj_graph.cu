@@ -2,17 +2,22 @@
 //
 // Input: an undirected edge list (src, dst, w), each edge once.  Every edge
 // e = (u, v) yields two directed entries, (row u, col v) and (row v, col u),
-// numbered 2e and 2e+1.  A stable LSD radix sort of the 2m entries by row
-// id gives a CSR whose rows keep the input order of their entries, so the
-// graph (and every sum over it) is the same bits on every upload.  Self-loops
-// get the key n and sort past the last row, i.e. they are dropped
-// (b_e = e_i - e_i = 0 contributes nothing to L).
+// numbered 2e and 2e+1.  Self-loops contribute nothing to L
+// (b_e = e_i - e_i = 0) and are dropped.
 //
-// The nodes are then renumbered by decreasing degree (a stable radix sort of
-// saturated degree keys), the CSR is rewritten in that order, and the SpMV
-// layouts are derived from it: chunks of the long rows, sliced ELL for the
-// rest, the static work partition, the merge-path tile plan and the Jacobi
-// preconditioner 1 / (1 + d_i).
+//   1. one pass over the edges validates them and counts node degrees;
+//   2. nodes are renumbered by decreasing degree (a stable radix sort of
+//      saturated degree keys), which fixes the solver-order row pointers and
+//      the SpMV layouts: chunks of the long rows, sliced ELL for the rest,
+//      and the work units;
+//   3. a stable LSD radix sort of the 2m entries by solver-order row puts
+//      every entry at its CSR position, rows keeping the input order of their
+//      entries, and its last pass also writes the sliced-ELL copy;
+//   4. the Jacobi preconditioner 1 / (1 + d_i).
+// The graph, and every sum over it, is therefore the same bits on every
+// upload.  The host waits once, at the end, for the sizes and the
+// validation result; invalid edges are treated as self-loops until then, so
+// no kernel indexes out of range.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -31,9 +36,9 @@ constexpr int kScanChunk = kScanThreads * kScanItems;
 
 // ------------------------------------------------------------ validation
 
-__global__ void k_validate(int64_t m, int64_t n, const int32_t* __restrict__ src,
-                           const int32_t* __restrict__ dst, const float* __restrict__ w,
-                           int* __restrict__ err, unsigned long long* __restrict__ first_bad) {
+__global__ void k_validate_degree(int64_t m, int64_t n, const int32_t* __restrict__ src,
+                                  const int32_t* __restrict__ dst, const float* __restrict__ w,
+                                  int64_t* __restrict__ err, int32_t* __restrict__ deg) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t u = src[e], v = dst[e];
@@ -44,20 +49,25 @@ __global__ void k_validate(int64_t m, int64_t n, const int32_t* __restrict__ src
       if (!(x > 0.0f) || isinf(x)) bad |= kErrBadWeight;
     }
     if (bad) {
-      atomicOr(err, bad);
-      atomicMin(first_bad, (unsigned long long)e);
+      atomicOr(reinterpret_cast<unsigned long long*>(&err[0]), (unsigned long long)bad);
+      atomicMin(reinterpret_cast<unsigned long long*>(&err[1]), (unsigned long long)e);
+    } else if (u != v) {
+      atomicAdd(&deg[u], 1);
+      atomicAdd(&deg[v], 1);
     }
   }
 }
 
 // ------------------------------------------------------------- radix sort
 
-// One directed entry: key = row id (n for a self-loop), col, weight.
+// One directed entry: key = solver-order row id (n for a self-loop or an
+// invalid edge), col = solver-order column, weight.
 struct EntrySrc {
-  const int32_t* src;  // edge list (first pass) ...
+  const int32_t* src;      // edge list (first pass) ...
   const int32_t* dst;
   const float* w;
-  const int32_t* key;  // ... or sorted arrays (later passes)
+  const int32_t* old2new;  // input id -> solver id
+  const int32_t* key;      // ... or sorted arrays (later passes)
   const int32_t* col;
   const float* val;
   int32_t n;
@@ -70,9 +80,9 @@ __device__ __forceinline__ void load_entry(const EntrySrc& s, int64_t p, int32_t
     const int64_t e = p >> 1;
     const int32_t u = s.src[e], v = s.dst[e];
     const bool side = p & 1;
-    key = side ? v : u;
-    col = side ? u : v;
-    if (u == v) key = s.n;
+    const bool ok = u != v && u >= 0 && u < s.n && v >= 0 && v < s.n;
+    key = ok ? s.old2new[side ? v : u] : s.n;
+    col = ok ? s.old2new[side ? u : v] : 0;
     val = s.w ? s.w[e] : 1.0f;
   } else {
     key = s.key[p];
@@ -80,6 +90,18 @@ __device__ __forceinline__ void load_entry(const EntrySrc& s, int64_t p, int32_t
     val = s.val ? s.val[p] : 1.0f;
   }
 }
+
+// Where the last pass of the entry sort writes: the CSR (sorted position =
+// CSR position) and, for rows past the long ones, the sliced ELL.
+struct EntryDst {
+  int32_t* col;
+  float* val;
+  const int32_t* row_ptr;
+  const int64_t* cnt;  // cnt[0] = n_long
+  const int64_t* slice_off;
+  int32_t* sell_col;
+  float* sell_val;
+};
 
 template <bool FROM_EDGES>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t N, int shift,
@@ -104,7 +126,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t
 // Stable scatter of one chunk of kSortChunk items.  Items are ranked in
 // input order (rounds of kSortThreads items: by warp, then by lane), placed
 // in shared memory in digit order, and written out as one contiguous run per
-// digit, so that global stores are coalesced.
+// digit, so that global stores are coalesced.  LAST: the sorted position is
+// the entry's CSR position; write the CSR and sliced-ELL copies instead of
+// the sort buffers (entries keyed n are dropped).
 struct ScatterSmem {
   int32_t key[kSortChunk];
   int32_t col[kSortChunk];
@@ -114,12 +138,12 @@ struct ScatterSmem {
   int start[256];
 };
 
-template <bool FROM_EDGES>
+template <bool FROM_EDGES, bool LAST>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int64_t N, int shift,
                                                                 const int32_t* __restrict__ offs,
                                                                 int32_t* __restrict__ okey,
                                                                 int32_t* __restrict__ ocol,
-                                                                float* __restrict__ oval) {
+                                                                float* __restrict__ oval, EntryDst d) {
   constexpr int kW = kSortThreads / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
@@ -197,13 +221,29 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
     }
   }
   __syncthreads();
+  const int64_t n_long = LAST ? d.cnt[0] : 0;
   for (int i = tid; i < cnt; i += kSortThreads) {
     const int32_t k = sm.key[i];
     const int digit = (k >> shift) & 255;
     const int64_t pos = (int64_t)offs[(int64_t)digit * gridDim.x + blockIdx.x] + (i - sm.start[digit]);
-    okey[pos] = k;
-    ocol[pos] = sm.col[i];
-    if (oval) oval[pos] = sm.val[i];
+    if (LAST) {
+      if (k < s.n) {
+        const int32_t c = sm.col[i];
+        const float v = sm.val[i];
+        d.col[pos] = c;
+        if (d.val) d.val[pos] = v;
+        if (k >= n_long) {
+          const int64_t sr = k - n_long;
+          const int64_t sp = d.slice_off[sr >> 5] + 32 * (pos - d.row_ptr[k]) + (sr & 31);
+          d.sell_col[sp] = c;
+          if (d.sell_val) d.sell_val[sp] = v;
+        }
+      }
+    } else {
+      okey[pos] = k;
+      ocol[pos] = sm.col[i];
+      if (oval) oval[pos] = sm.val[i];
+    }
   }
 }
 
@@ -299,18 +339,6 @@ static fj_status exclusive_scan(T* data, int64_t cnt, cudaStream_t st) {
 
 // ------------------------------------------------------------ CSR pieces
 
-// row_ptr[r] = first sorted position whose key >= r, for r in [0, n].
-__global__ void k_row_ptr(const int32_t* __restrict__ key, int64_t N, int64_t n,
-                          int32_t* __restrict__ row_ptr) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= N;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t kp = (p < N) ? key[p] : n;
-    const int64_t kprev = (p > 0) ? key[p - 1] : -1;
-    const int64_t hi = kp < n ? kp : n;
-    for (int64_t r = kprev + 1; r <= hi; ++r) row_ptr[r] = (int32_t)p;
-  }
-}
-
 __global__ void k_dinv_unit(const int32_t* __restrict__ row_ptr, int64_t n, float* __restrict__ dinv) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -321,19 +349,19 @@ __global__ void k_dinv_unit(const int32_t* __restrict__ row_ptr, int64_t n, floa
 // ------------------------------------------------------- solver order
 
 // Sort key of node i: decreasing degree (saturated), payload i.
-__global__ void k_degree_keys(const int32_t* __restrict__ row_ptr, int64_t n, int32_t* __restrict__ key,
+__global__ void k_degree_keys(const int32_t* __restrict__ deg, int64_t n, int32_t* __restrict__ key,
                               int32_t* __restrict__ id) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t d = row_ptr[i + 1] - row_ptr[i];
+    const int32_t d = deg[i];
     key[i] = kDegKeyMax - (d < kDegKeyMax ? d : kDegKeyMax);
     id[i] = (int32_t)i;
   }
 }
 
 // old2new[perm[i]] = i; deg_new[i] = degree of perm[i] (into rp_new[i]).
-__global__ void k_apply_perm(const int32_t* __restrict__ perm, const int32_t* __restrict__ row_ptr_old,
-                             int64_t n, int32_t* __restrict__ old2new, int32_t* __restrict__ rp_new) {
+__global__ void k_apply_perm(const int32_t* __restrict__ perm, const int32_t* __restrict__ deg, int64_t n,
+                             int32_t* __restrict__ old2new, int32_t* __restrict__ rp_new) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (i == n) {
@@ -341,38 +369,7 @@ __global__ void k_apply_perm(const int32_t* __restrict__ perm, const int32_t* __
     } else {
       const int32_t o = perm[i];
       old2new[o] = (int32_t)i;
-      rp_new[i] = row_ptr_old[o + 1] - row_ptr_old[o];
-    }
-  }
-}
-
-// Entry p of the row-sorted input CSR moves to its place in the solver-order
-// CSR (same position inside its row), with the column renumbered; entries
-// of short rows also go to their sliced-ELL position.
-__global__ void k_copy_entries(const int32_t* __restrict__ key, const int32_t* __restrict__ col_old,
-                               const float* __restrict__ val_old, int64_t n,
-                               const int32_t* __restrict__ row_ptr_old, const int32_t* __restrict__ old2new,
-                               const int32_t* __restrict__ row_ptr_new, int32_t* __restrict__ col_new,
-                               float* __restrict__ val_new, const int64_t* __restrict__ cnt,
-                               const int64_t* __restrict__ slice_off, int32_t* __restrict__ sell_col,
-                               float* __restrict__ sell_val) {
-  const int64_t nnz = row_ptr_old[n];  // entries past nnz are self-loops (key n)
-  const int64_t n_long = cnt[0];
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t ro = key[p];
-    const int32_t o = (int32_t)p - row_ptr_old[ro];
-    const int32_t rn = old2new[ro];
-    const int32_t pn = row_ptr_new[rn] + o;
-    const int32_t c = old2new[col_old[p]];
-    const float w = val_old ? val_old[p] : 1.0f;
-    col_new[pn] = c;
-    if (val_new) val_new[pn] = w;
-    if (rn >= n_long) {
-      const int64_t sr = rn - n_long;
-      const int64_t pos = slice_off[sr >> 5] + 32 * (int64_t)o + (sr & 31);
-      sell_col[pos] = c;
-      if (sell_val) sell_val[pos] = w;
+      rp_new[i] = deg[o];
     }
   }
 }
@@ -419,12 +416,17 @@ __global__ void k_layout_sizes(const int32_t* __restrict__ row_ptr, int64_t n, i
 // Fills the chunk table and the work-unit costs: unit_cost[c] for chunk c,
 // unit_cost[n_chunks + s] for slice s, 0 beyond (the array is sized by an
 // upper bound and scanned over all of it).
-__global__ void k_units(const int32_t* __restrict__ row_ptr, const int64_t* __restrict__ cnt,
+// Also completes the sizes: cnt[4] = n_chunks, cnt[5] = sliced-ELL entries.
+__global__ void k_units(const int32_t* __restrict__ row_ptr, int64_t* __restrict__ cnt,
                         const int32_t* __restrict__ long_first, const int64_t* __restrict__ slice_off,
                         int64_t units_cap, int32_t* __restrict__ chunk_row, int32_t* __restrict__ chunk_begin,
                         int32_t* __restrict__ chunk_end, int64_t* __restrict__ unit_cost) {
   const int64_t n_long = cnt[0], n_slices = cnt[2];
   const int64_t n_chunks = long_first[n_long];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cnt[4] = n_chunks;
+    cnt[5] = slice_off[n_slices];
+  }
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_long;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int32_t b = row_ptr[r], e = row_ptr[r + 1];
@@ -522,19 +524,6 @@ __global__ void k_dinv_weighted(const int32_t* __restrict__ row_ptr, int64_t n, 
   }
 }
 
-// Merge-path row coordinate of every tile start, for nnz read on the device.
-__global__ void k_tile_rows_dev(const int32_t* __restrict__ row_ptr, int64_t n, int64_t tiles_cap,
-                                int32_t* __restrict__ tile_row) {
-  const int64_t nnz = row_ptr[n];
-  const int64_t n_tiles = (n + nnz + kTileItems - 1) / kTileItems;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= tiles_cap && t <= n_tiles;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t d = t * kTileItems;
-    if (d > n + nnz) d = n + nnz;
-    tile_row[t] = (int32_t)merge_path_row(row_ptr, n, d);
-  }
-}
-
 static unsigned grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -545,9 +534,11 @@ static unsigned grid_for(int64_t work, int threads) {
 // Stable LSD radix sort (8-bit digits) of N entries by key in [0, key_max].
 // FROM_EDGES: entries are generated from the edge list (first pass only).
 // Buffers kb/cb/vb[2] must hold N + kPad elements (vb may be null: no val);
-// returns the index (0/1) of the buffer set holding the result.
+// returns the index (0/1) of the buffer set holding the result.  With
+// `last`, the last pass writes the CSR and sliced ELL instead.
 static fj_status radix_sort(EntrySrc src, bool from_edges, int64_t N, int64_t key_max, int32_t* kb[2],
-                            int32_t* cb[2], float* vb[2], cudaStream_t st, int* result) {
+                            int32_t* cb[2], float* vb[2], const EntryDst* last, cudaStream_t st,
+                            int* result) {
   int bits = 1;
   while ((int64_t(1) << bits) <= key_max) ++bits;
   const int passes = (bits + 7) / 8;
@@ -558,8 +549,11 @@ static fj_status radix_sort(EntrySrc src, bool from_edges, int64_t N, int64_t ke
   int32_t* h = nullptr;
   FJ_CUDA(malloc_async(&h, 256 * nblocks * sizeof(int32_t), st));
   fj_status rc = FJ_OK;
+  const size_t ssm = sizeof(ScatterSmem);
+  const EntryDst none{};
   for (int pass = 0; pass < passes && rc == FJ_OK; ++pass) {
     const bool edges = from_edges && pass == 0;
+    const bool fin = last && pass == passes - 1;
     EntrySrc s = src;
     if (!edges) {
       s.key = kb[cur];
@@ -567,23 +561,27 @@ static fj_status radix_sort(EntrySrc src, bool from_edges, int64_t N, int64_t ke
       s.val = vb[cur];
     }
     const int dstb = edges ? 0 : 1 - cur;
+    const int shift = pass * 8;
     count_launches(2);
-    if (edges) {
-      k_radix_hist<true><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, 0, h);
-    } else {
-      k_radix_hist<false><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, pass * 8, h);
-    }
+    if (edges)
+      k_radix_hist<true><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, shift, h);
+    else
+      k_radix_hist<false><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, shift, h);
     rc = exclusive_scan<int32_t>(h, 256 * nblocks, st);
     if (rc != FJ_OK) break;
-    const size_t ssm = sizeof(ScatterSmem);
-    if (edges) {
-      cudaFuncSetAttribute(k_radix_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
-      k_radix_scatter<true><<<(unsigned)nblocks, kSortThreads, ssm, st>>>(s, N, 0, h, kb[dstb], cb[dstb], vb[dstb]);
-    } else {
-      cudaFuncSetAttribute(k_radix_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
-      k_radix_scatter<false><<<(unsigned)nblocks, kSortThreads, ssm, st>>>(s, N, pass * 8, h, kb[dstb], cb[dstb],
-                                                                          vb[dstb]);
-    }
+    const EntryDst& d = fin ? *last : none;
+    auto launch = [&](auto kern) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+      kern<<<(unsigned)nblocks, kSortThreads, ssm, st>>>(s, N, shift, h, kb[dstb], cb[dstb], vb[dstb], d);
+    };
+    if (edges && fin)
+      launch(k_radix_scatter<true, true>);
+    else if (edges)
+      launch(k_radix_scatter<true, false>);
+    else if (fin)
+      launch(k_radix_scatter<false, true>);
+    else
+      launch(k_radix_scatter<false, false>);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "radix sort");
     cur = dstb;
@@ -629,9 +627,9 @@ struct Pool {
 }  // namespace
 
 void fj_free_graph_arrays(fj_graph* g, cudaStream_t st) {
-  void* arrays[] = {g->row_ptr,     g->col,       g->val,       g->dinv,      g->tile_row,
-                    g->perm,        g->long_first, g->chunk_row, g->chunk_begin, g->chunk_end,
-                    g->slice_off,   g->sell_col,  g->sell_val,  g->unit_prefix};
+  void* arrays[] = {g->row_ptr,     g->col,       g->val,         g->dinv,      g->perm,
+                    g->long_first,  g->chunk_row, g->chunk_begin, g->chunk_end, g->slice_off,
+                    g->sell_col,    g->sell_val,  g->unit_prefix};
   for (void* p : arrays)
     if (p) cudaFreeAsync(p, st);
 }
@@ -643,58 +641,25 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   const int64_t N = 2 * m;
   const bool weighted = (w != nullptr);
   Pool pool(st);
-  // ---- validation
-  int* err = pool.get<int>(4);
-  if (!err) {
-    set_error("fj_graph_upload: out of device memory");
-    return FJ_ERR_OOM;
-  }
-  unsigned long long* first_bad = (unsigned long long*)(err + 2);
-  FJ_CUDA(cudaMemsetAsync(err, 0, 4, st));
-  FJ_CUDA(cudaMemsetAsync(first_bad, 0xff, 8, st));
-  if (m > 0) {
-    count_launches(1);
-    k_validate<<<grid_for(m, 256), 256, 0, st>>>(m, n, src, dst, w, err, first_bad);
-    FJ_CUDA(cudaGetLastError());
-  }
-  int herr = 0;
-  unsigned long long hbad = 0;
-  FJ_CUDA(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
-  FJ_CUDA(cudaMemcpyAsync(&hbad, first_bad, 8, cudaMemcpyDeviceToHost, st));
-  FJ_CUDA(cudaStreamSynchronize(st));
-  if (herr) {
-    set_error("fj_graph_upload: edge %llu has %s", hbad,
-              (herr & kErrBadId) ? "a node id outside [0, n)" : "a weight that is not finite and > 0");
-    return FJ_ERR_GRAPH;
-  }
   auto oom = [&]() {
     set_error("fj_graph_upload: out of device memory (n=%lld, m=%lld)", (long long)n, (long long)m);
     return FJ_ERR_OOM;
   };
-
-  // ---- 1. input-order CSR by a stable sort of the directed entries by row
-  const int64_t cap = std::max<int64_t>(N, n) + kPad;
-  int32_t* kb[2];
-  int32_t* cb[2];
-  float* vb[2] = {nullptr, nullptr};
-  for (int i = 0; i < 2; ++i) {
-    kb[i] = pool.get<int32_t>(cap);
-    cb[i] = pool.get<int32_t>(cap);
-    if (weighted) vb[i] = pool.get<float>(cap);
-  }
+  // dcnt: [0] n_long [1] n_nz [2] n_slices [3] nnz [4] n_chunks [5] sliced-ELL
+  // entries [6] validation error bits [7] first invalid edge
+  int64_t* dcnt = pool.get<int64_t>(8);
+  int32_t* deg = pool.get<int32_t>(n);
   if (pool.failed) return oom();
-  EntrySrc es{src, dst, w, nullptr, nullptr, nullptr, (int32_t)n};
-  int cur = 0;
-  fj_status rc = radix_sort(es, true, N, n, kb, cb, vb, st, &cur);
-  if (rc != FJ_OK) return rc;
-  int32_t* key_old = kb[cur];
-  int32_t* col_old = cb[cur];
-  float* val_old = vb[cur];
-  int32_t* rp_old = pool.get<int32_t>(n + 1);
-  if (!rp_old) return oom();
-  count_launches(1);
-  k_row_ptr<<<grid_for(N + 1, 256), 256, 0, st>>>(key_old, N, n, rp_old);
-  FJ_CUDA(cudaGetLastError());
+  FJ_CUDA(cudaMemsetAsync(dcnt, 0, 56, st));
+  FJ_CUDA(cudaMemsetAsync(dcnt + 7, 0xff, 8, st));
+  FJ_CUDA(cudaMemsetAsync(deg, 0, n * sizeof(int32_t), st));
+
+  // ---- 1. validation and degrees
+  if (m > 0) {
+    count_launches(1);
+    k_validate_degree<<<grid_for(m, 256), 256, 0, st>>>(m, n, src, dst, w, dcnt + 6, deg);
+    FJ_CUDA(cudaGetLastError());
+  }
 
   // ---- 2. solver order: stable sort of nodes by decreasing degree
   int32_t* kb2[2] = {pool.get<int32_t>(n + kPad), pool.get<int32_t>(n + kPad)};
@@ -702,11 +667,11 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   float* vb2[2] = {nullptr, nullptr};
   if (pool.failed) return oom();
   count_launches(1);
-  k_degree_keys<<<grid_for(n, 256), 256, 0, st>>>(rp_old, n, kb2[0], cb2[0]);
+  k_degree_keys<<<grid_for(n, 256), 256, 0, st>>>(deg, n, kb2[0], cb2[0]);
   FJ_CUDA(cudaGetLastError());
-  EntrySrc ns{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, (int32_t)n};
+  EntrySrc ns{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, (int32_t)n};
   int cur2 = 0;
-  rc = radix_sort(ns, false, n, kDegKeyMax, kb2, cb2, vb2, st, &cur2);
+  fj_status rc = radix_sort(ns, false, n, kDegKeyMax, kb2, cb2, vb2, nullptr, st, &cur2);
   if (rc != FJ_OK) return rc;
   int32_t* perm = cb2[cur2];
 
@@ -724,14 +689,13 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   g->perm = perm;
   pool.keep(perm);
   int32_t* old2new = pool.get<int32_t>(n);
-  g->row_ptr = (int32_t*)nullptr;
   if (malloc_async(&g->row_ptr, (n + 1) * sizeof(int32_t), st) != cudaSuccess || !old2new) {
     cudaGetLastError();
     g->row_ptr = nullptr;
     return fail(oom());
   }
   count_launches(1);
-  k_apply_perm<<<grid_for(n + 1, 256), 256, 0, st>>>(perm, rp_old, n, old2new, g->row_ptr);
+  k_apply_perm<<<grid_for(n + 1, 256), 256, 0, st>>>(perm, deg, n, old2new, g->row_ptr);
   rc = exclusive_scan<int32_t>(g->row_ptr, n + 1, st);
   if (rc != FJ_OK) return fail(rc);
 
@@ -745,9 +709,6 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   const int64_t nc_cap = nl_cap + N / kChunkLen + 1;
   const int64_t units_cap = nc_cap + ns_cap;
   const int64_t sell_cap = N + 32 * kSellMaxLen;
-  int64_t* dcnt = pool.get<int64_t>(8);
-  if (!dcnt) return fail(oom());
-  cudaMemsetAsync(dcnt, 0, 64, st);
   if (malloc_async(&g->col, (N + kPad) * 4, st) != cudaSuccess ||
       (weighted && malloc_async(&g->val, (N + kPad) * 4, st) != cudaSuccess) ||
       malloc_async(&g->slice_off, (ns_cap + 1) * 8, st) != cudaSuccess ||
@@ -761,8 +722,9 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
     cudaGetLastError();
     return fail(oom());
   }
-  cudaMemsetAsync(g->col, 0, (N + kPad) * 4, st);
-  if (weighted) cudaMemsetAsync(g->val, 0, (N + kPad) * 4, st);
+  // the padding past nnz is read by batched loads (never used)
+  cudaMemsetAsync(g->col + N, 0, kPad * 4, st);
+  if (weighted) cudaMemsetAsync(g->val + N, 0, kPad * 4, st);
   count_launches(2);
   k_count_long<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, dcnt);
   k_layout_sizes<<<grid_for(ns_cap + nl_cap + 2, 256), 256, 0, st>>>(g->row_ptr, n, dcnt, ns_cap, nl_cap,
@@ -770,34 +732,49 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   rc = exclusive_scan<int64_t>(g->slice_off, ns_cap + 1, st);
   if (rc == FJ_OK) rc = exclusive_scan<int32_t>(g->long_first, nl_cap + 1, st);
   if (rc != FJ_OK) return fail(rc);
-  count_launches(3);
+  count_launches(2);
   k_units<<<grid_for(std::max(nl_cap, units_cap + 1), 256), 256, 0, st>>>(
       g->row_ptr, dcnt, g->long_first, g->slice_off, units_cap, g->chunk_row, g->chunk_begin, g->chunk_end,
       g->unit_prefix);
   k_sell_pad<<<grid_for(ns_cap * 32, 256), 256, 0, st>>>(g->row_ptr, n, dcnt, g->slice_off, g->sell_col,
                                                          g->sell_val);
-  // ---- 4. entries to the solver-order CSR and the sliced ELL
-  k_copy_entries<<<grid_for(N, 256), 256, 0, st>>>(key_old, col_old, val_old, n, rp_old, old2new, g->row_ptr,
-                                                   g->col, g->val, dcnt, g->slice_off, g->sell_col, g->sell_val);
   if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
   rc = exclusive_scan<int64_t>(g->unit_prefix, units_cap + 1, st);
   if (rc != FJ_OK) return fail(rc);
 
-  // ---- 5. merge-path tile plan and Jacobi preconditioner
-  const int64_t tiles_cap = (n + N + kTileItems - 1) / kTileItems;
-  if (malloc_async(&g->tile_row, (tiles_cap + 1) * sizeof(int32_t), st) != cudaSuccess ||
-      malloc_async(&g->dinv, n * sizeof(float), st) != cudaSuccess) {
+  // ---- 4. entries, sorted by solver-order row, straight to the CSR and the
+  // sliced ELL
+  {
+    const int64_t cap = N + kPad;
+    int32_t* kb[2];
+    int32_t* cb[2];
+    float* vb[2] = {nullptr, nullptr};
+    Pool sort_pool(st);
+    for (int i = 0; i < 2; ++i) {
+      kb[i] = sort_pool.get<int32_t>(cap);
+      cb[i] = sort_pool.get<int32_t>(cap);
+      if (weighted) vb[i] = sort_pool.get<float>(cap);
+    }
+    if (sort_pool.failed) return fail(oom());
+    EntrySrc es{src, dst, w, old2new, nullptr, nullptr, nullptr, (int32_t)n};
+    EntryDst ed{g->col, g->val, g->row_ptr, dcnt, g->slice_off, g->sell_col, g->sell_val};
+    int cur = 0;
+    rc = radix_sort(es, true, N, n, kb, cb, vb, &ed, st, &cur);
+    if (rc != FJ_OK) return fail(rc);
+  }
+
+  // ---- 5. Jacobi preconditioner
+  if (malloc_async(&g->dinv, n * sizeof(float), st) != cudaSuccess) {
     cudaGetLastError();
     return fail(oom());
   }
-  count_launches(2);
-  k_tile_rows_dev<<<grid_for(tiles_cap + 1, 256), 256, 0, st>>>(g->row_ptr, n, tiles_cap, g->tile_row);
+  count_launches(1);
   if (!weighted) {
     k_dinv_unit<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, g->dinv);
   } else {
     float* cpart = pool.get<float>(nc_cap);
     if (!cpart) return fail(oom());
-    count_launches(2);
+    count_launches(1);
     k_chunk_wsum<<<grid_for(nc_cap * 32, 256), 256, 0, st>>>(g->val, g->long_first, dcnt, g->chunk_begin,
                                                              g->chunk_end, cpart);
     k_dinv_weighted<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, dcnt, g->long_first, cpart, g->slice_off,
@@ -805,23 +782,23 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   }
   if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
 
-  // ---- sizes back to the host (the one round trip after validation)
-  int64_t hc[4] = {0, 0, 0, 0};
-  int32_t hch = 0;
-  if (cudaMemcpyAsync(hc, dcnt, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+  // ---- sizes and the validation result back to the host (one round trip)
+  int64_t hc[8];
+  if (cudaMemcpyAsync(hc, dcnt, sizeof(hc), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return fail(FJ_ERR_CUDA);
-  if (cudaMemcpyAsync(&hch, g->long_first + hc[0], 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaMemcpyAsync(&g->sell_nnz, g->slice_off + hc[2], 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return fail(FJ_ERR_CUDA);
+  if (hc[6]) {
+    set_error("fj_graph_upload: edge %llu has %s", (unsigned long long)hc[7],
+              (hc[6] & kErrBadId) ? "a node id outside [0, n)" : "a weight that is not finite and > 0");
+    return fail(FJ_ERR_GRAPH);
+  }
   g->n_long = hc[0];
   g->n_nz = std::max(hc[1], hc[0]);
   g->n_slices = hc[2];
   g->nnz = hc[3];
-  g->n_chunks = hch;
+  g->n_chunks = hc[4];
+  g->sell_nnz = hc[5];
   g->n_units = g->n_chunks + g->n_slices;
-  g->n_tiles = (n + g->nnz + kTileItems - 1) / kTileItems;
   *out = g;
   return FJ_OK;
 }

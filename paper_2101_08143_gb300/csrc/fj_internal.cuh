@@ -6,7 +6,6 @@
 //   row_ptr/col/val  CSR of the off-diagonal part of L in solver order,
 //                    each row's entries in input-edge order
 //   dinv             1 / (1 + d_i), the Jacobi preconditioner
-//   tile_row         merge-path row coordinate of every kTileItems tile
 //   rows [0, n_long) with more than kSellMaxLen entries ("long rows") are cut
 //                    into chunks of at most kChunkLen entries
 //   rows [n_long, n_nz) are stored as sliced ELL (rows [n_nz, n) have no
@@ -26,11 +25,8 @@
 
 namespace fj {
 
-// Merge-path items (row ends + nonzeros) per warp tile: 7 per lane, sized
-// so that two 16-warp blocks with float64 tile staging fit one SM.
-constexpr int kTileItems = 224;
-// Extra zeroed elements after col/val so that staging loads of the last tile
-// never leave the allocation.
+// Extra elements after the sort buffers and col/val (batched loads past the
+// last entry stay inside the allocation).
 constexpr int kPad = 64;
 // Rows with at most kSellMaxLen entries go to sliced ELL; longer rows are
 // processed warp-wide in chunks of at most kChunkLen entries.
@@ -59,14 +55,12 @@ struct fj_graph {
   int device;
   int64_t n;
   int64_t nnz;
-  int64_t n_tiles;
   int weighted;
   // CSR in solver order
   int32_t* row_ptr;
   int32_t* col;
   float* val;
   float* dinv;
-  int32_t* tile_row;
   int32_t* perm;  // perm[i] = input id of solver node i
   // long rows [0, n_long) in chunks; rows [n_nz, n) have no entries
   int64_t n_long;
@@ -105,22 +99,6 @@ __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-// Largest r in [lo, hi] with f(r) = row_ptr[r] + r <= d (merge-path split of
-// diagonal d between the row-end list and the nonzero list).
-__device__ __forceinline__ int64_t merge_path_row(const int32_t* row_ptr,
-                                                  int64_t n, int64_t d) {
-  int64_t lo = 0, hi = n;
-  if (hi > d) hi = d;
-  while (lo < hi) {
-    int64_t mid = (lo + hi + 1) >> 1;
-    if ((int64_t)row_ptr[mid] + mid <= d)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
 }
 
 }  // namespace fj

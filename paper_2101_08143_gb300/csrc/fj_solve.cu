@@ -54,8 +54,7 @@ enum Mode { kModeMixed = 0, kModeFP64 = 1, kModeFP32 = 2 };
 
 template <typename VI>
 struct SolveParams {
-  WalkGraph g;   // merge-path view (K >= 8)
-  SellGraph sg;  // sliced-ELL view (K <= 4)
+  SellGraph sg;  // work units: long-row chunks and 32-row slices
   const int32_t* perm;  // solver node -> input id
   VI* hub_part;         // [n_chunks][K] chunk sums of multi-chunk rows
   df64* hub_part64;
@@ -80,9 +79,6 @@ struct SolveParams {
   VI* p;
   VI* d;
   VI* t;
-  int32_t* wc_row;
-  VI* wc_val;
-  df64* wc_val64;
   double* part;  // [gridDim][NSLOT][K]
   Barrier* bar;
   // options
@@ -234,10 +230,6 @@ __device__ __forceinline__ double lane_share(T (&v)[K]) {
 template <typename VI, int K>
 __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // per-warp tile staging, sized for the widest walk of this launch
-  constexpr size_t kTileBytes = tile_smem_bytes<VI, K>() > tile_smem_bytes<double, K>()
-                                    ? tile_smem_bytes<VI, K>()
-                                    : tile_smem_bytes<double, K>();
   double* red = reinterpret_cast<double*>(smem_raw);  // [7][kWarps][K], aliases the staging
   __shared__ double res[NSLOT * K];
   __shared__ double alpha[K], beta[K], gam_prev[K], alpha_prev[K], rr_goal[K], mu[K], bb[K];
@@ -245,14 +237,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   __shared__ int ctl_any_active, ctl_stop;
 
   const int warp = threadIdx.x >> 5;
-  const int64_t n = P.g.n;
+  const int64_t n = P.sg.n;
   const int64_t NK = n * K;
   const int64_t gtid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * kThreads;
   const int c = threadIdx.x % K;
   const int64_t wg = (int64_t)blockIdx.x * kWarps + warp;
   // per-warp staging of the wide walks' row values
-  VI* my_sxr = reinterpret_cast<VI*>(smem_raw + warp * kGatherBytesPerWarp);
+  VI* my_sxr = reinterpret_cast<VI*>(smem_raw + warp * kWideStageBytes);
   df64* my_sxr64 = reinterpret_cast<df64*>(my_sxr);
   int* status = P.status;
   const bool fp32_mode = P.mode == kModeFP32;
@@ -616,18 +608,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
 
 // ------------------------------------------------------------------ host
 
-struct LaunchShape {
-  int blocks;
-  int64_t tiles_per_warp;
-};
-
 template <typename VI, int K>
 static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, const double* s,
                             int64_t ld, double* z, double* quant, double* resid, int* status,
                             char* ws, size_t ws_bytes, const fj_opts& o, int mode, int max_blocks) {
   auto kern = k_solve<VI, K>;
   const size_t red_bytes = (size_t)7 * kWarps * K * sizeof(double);
-  const size_t stage = (K <= 4) ? 0 : (size_t)kWarps * kGatherBytesPerWarp;
+  const size_t stage = (K <= 4) ? 0 : (size_t)kWarps * kWideStageBytes;
   const size_t dyn = std::max(red_bytes, stage);
   FJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int per_sm = 0;
@@ -645,8 +632,6 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   int64_t cap = (int64_t)std::min(per_sm, kMaxBlocksPerSM) * num_sms;
   if (max_blocks > 0 && cap > max_blocks) cap = max_blocks;
   const int blocks = (int)std::min(want, cap);
-  const int64_t warps = (int64_t)blocks * kWarps;
-  const int64_t tpw = std::max<int64_t>(1, (g->n_tiles + warps - 1) / warps);
 
   // carve the workspace
   const int64_t NK = n * K;
@@ -657,8 +642,6 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
     return (void*)p;
   };
   SolveParams<VI> P;
-  P.g = WalkGraph{g->row_ptr, g->col, g->val, g->tile_row, n, g->nnz, g->n_tiles, tpw, {}};
-  set_tiles_per_warp(P.g, tpw);
   P.sg = SellGraph{g->row_ptr,   g->col,       g->val,      g->long_first, g->chunk_row,
                    g->chunk_begin, g->chunk_end, g->slice_off, g->sell_col,   g->sell_val,
                    g->unit_prefix, n,            g->n_long,   g->n_nz,       g->n_chunks,
@@ -680,9 +663,6 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.p = (VI*)take(NK * sizeof(VI));
   P.d = (VI*)take(NK * sizeof(VI));
   P.t = (VI*)take(NK * sizeof(VI));
-  P.wc_row = (int32_t*)take(warps * 4);
-  P.wc_val = (VI*)take(warps * K * sizeof(VI));
-  P.wc_val64 = (df64*)take(warps * K * 8);
   P.part = (double*)take((size_t)blocks * NSLOT * K * 8);
   P.hub_part = (VI*)take(std::max<int64_t>(g->n_chunks, 1) * K * sizeof(VI));
   P.hub_part64 = (df64*)take(std::max<int64_t>(g->n_chunks, 1) * K * 8);
@@ -714,16 +694,12 @@ using namespace fj;
 size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms) {
   const int64_t NK = g->n * (int64_t)K;
   const int64_t blocks = (int64_t)num_sms * kMaxBlocksPerSM;
-  const int64_t warps = blocks * kWarps;
   size_t b = 0;
   auto add = [&](size_t x) { b += (x + 255) & ~size_t(255); };
   add(NK * 8);
   add(NK * 8);
   add(NK * 8);
   for (int i = 0; i < 6; ++i) add(NK * inner_bytes);
-  add(warps * 4);
-  add(warps * K * inner_bytes);
-  add(warps * K * 8);
   add((size_t)blocks * NSLOT * K * 8);
   add(std::max<int64_t>(g->n_chunks, 1) * K * inner_bytes);
   add(std::max<int64_t>(g->n_chunks, 1) * K * 8);

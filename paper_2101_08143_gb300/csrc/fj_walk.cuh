@@ -1,25 +1,17 @@
-// fj_walk.cuh - load-balanced CSR row reductions ("walks") for libfj.
+// fj_walk.cuh - CSR row reductions ("walks") for libfj.
 //
 // The off-diagonal part of (I + L) x is t_i = sum_j w_ij (x_i - x_j), the
-// incidence form L = sum_e w_e b_e b_e^T of Sec. 2.1 evaluated row by row.
-// Power-law rows (hubs of 10^5..10^7 entries) make a row-per-thread or
-// row-per-warp split badly unbalanced, so every reduction over CSR rows here
-// walks the merge path of (row ends, nonzeros): the n + nnz path items are
-// cut into tiles of kTileItems items, each warp owns a contiguous run of
-// tiles, and inside a tile the items are split evenly between "walkers".
-//
-// A walker is K consecutive lanes handling K right-hand sides of one path
-// segment (K = 1: 32 walkers of one lane; K = 32: one walker of 32 lanes, so
-// every gathered row x_j is one coalesced 128-byte line).  Rows that cross
-// walker, tile or warp boundaries are combined deterministically:
-//   * walkers of one tile: a segmented shuffle scan keyed by row id;
-//   * tiles of one warp: the running carry stays in registers;
-//   * warps: each warp publishes its final carry; the consumer of row i adds
-//     the carries of the warps that end inside row i, in warp order.
-// The result is bit-reproducible for a fixed graph and launch shape.
+// incidence form L = sum_e w_e b_e b_e^T of Sec. 2.1 evaluated row by row,
+// and the walks also return sum over CSR entries of w_ij (x_i - x_j)^2
+// (= 2 x^T L x).  Nodes are in degree-descending order; rows of more than
+// kSellMaxLen entries are cut into chunks of at most kChunkLen entries, the
+// rest form 32-row slices.  Chunks, then slices, are the work units:
+//   K <= 4 columns  sliced ELL, one lane per row (sell_walk);
+//   K >= 8 columns  lanes as columns, each gathered row x_j one K-wide
+//                   coalesced load (wide_unit).
+// Every row sum is accumulated in entry order by one lane or combined in a
+// fixed order, so results are bit-reproducible.
 #pragma once
-
-#include <type_traits>
 
 #include "fj_df64.cuh"
 #include "fj_internal.cuh"
@@ -27,333 +19,6 @@
 namespace fj {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-// Per-warp shared staging for one tile.
-struct TileSmem {
-  int32_t re[kTileItems + 1];  // row_ptr[r0+1 .. r1+1]
-  int32_t col[kTileItems];
-  float val[kTileItems];
-};
-
-// Narrow right-hand sides (K * sizeof(T) <= 8) also stage the gathered
-// neighbour values x_j and the row values x_r of the tile, so that all of a
-// tile's gathers are in flight at once and the walk itself touches only
-// shared memory.
-template <typename T, int K>
-struct StagesX {
-  static constexpr bool value = K * sizeof(T) <= 8;
-};
-
-template <typename T, int K>
-struct TileSmemX {
-  int32_t re[kTileItems + 1];  // row_ptr[r0+1 .. r1+1]
-  float val[kTileItems];
-  T xj[kTileItems * K];        // x[col[k0 + j]]
-  T xr[(kTileItems + 1) * K];  // x[r0 + j]
-};
-
-template <typename T, int K>
-__host__ __device__ constexpr size_t tile_smem_bytes() {
-  return StagesX<T, K>::value ? sizeof(TileSmemX<T, K>) : sizeof(TileSmem);
-}
-
-// Unsigned 32-bit division by a run-time invariant d >= 1 with one multiply
-// (Granlund & Montgomery, "Division by invariant integers using
-// multiplication", PLDI 1994, Sec. 4): q = (t + ((a - t) >> 1)) >> (l - 1),
-// t = umulhi(m, a), l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1.
-struct FastDiv {
-  uint32_t d, m, s;  // s = l - 1 (d >= 2); d == 1 is handled apart
-  __host__ void init(uint32_t div) {
-    d = div;
-    uint32_t l = 0;
-    while ((uint64_t(1) << l) < div) ++l;
-    m = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - div)) / div + 1);
-    s = l ? l - 1 : 0;
-  }
-  __device__ __forceinline__ uint32_t div(uint32_t a) const {
-    if (d == 1) return a;
-    const uint32_t t = __umulhi(m, a);
-    return (t + ((a - t) >> 1)) >> s;
-  }
-};
-
-struct WalkGraph {
-  const int32_t* row_ptr;
-  const int32_t* col;
-  const float* val;  // nullptr: unit weights
-  const int32_t* tile_row;
-  int64_t n;
-  int64_t nnz;
-  int64_t n_tiles;
-  int64_t tiles_per_warp;
-  FastDiv items_per_warp;  // kTileItems * tiles_per_warp (n + nnz < 2^32)
-};
-
-inline void set_tiles_per_warp(WalkGraph& g, int64_t tpw) {
-  g.tiles_per_warp = tpw;
-  g.items_per_warp.init((uint32_t)(tpw * kTileItems));
-}
-
-enum WalkMode { kRowSum = 0, kLap = 1 };
-
-// Asynchronous 4/8-byte copies global -> shared (no registers held while
-// in flight); cp.async.wait_all makes the executing thread's copies visible.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-// Wide walks (K >= 8) prefetch the x rows of the next kPrefetch<T> nonzeros
-// of each walker into this much shared memory per warp.
-constexpr int kGatherBytesPerWarp = 4096;
-template <typename T>
-struct Prefetch {
-  static constexpr int value = kGatherBytesPerWarp / (32 * (int)sizeof(T));  // nonzeros per walker
-};
-
-// Walks tiles [wg*tpw, (wg+1)*tpw) of the merge path.
-//   kRowSum: out[r] = sum of row r's weights (K must be 1, x unused)
-//   kLap:    out[r*K+c] = sum_j w_rj (x[r*K+c] - x[j*K+c]); returns this
-//            lane's part of sum over entries of w (x_r - x_j)^2.
-// Rows wholly inside the warp's run are final in out[]; the run's last row
-// is published in wc_row[wg] / wc_val[wg*K + c] (carry of that row).
-template <typename T, int K, int MODE>
-__device__ __forceinline__ T walk_tiles(const WalkGraph& g, const T* __restrict__ x,
-                                        T* __restrict__ out, int32_t* __restrict__ wc_row,
-                                        T* __restrict__ wc_val, int64_t wg, void* smem,
-                                        T* __restrict__ gbuf = nullptr) {
-  constexpr bool kStageX = (MODE == kLap) && StagesX<T, K>::value;
-  // wide walks: x rows of upcoming nonzeros prefetched into gbuf (per walker)
-  constexpr bool kPre = (MODE == kLap) && !kStageX && K >= 8;
-  constexpr int PD = Prefetch<T>::value;
-  TileSmem* sm = reinterpret_cast<TileSmem*>(smem);
-  TileSmemX<T, K>* smx = reinterpret_cast<TileSmemX<T, K>*>(smem);
-  int32_t* s_re = kStageX ? smx->re : sm->re;
-  float* s_val = kStageX ? smx->val : sm->val;
-  constexpr int G = 32 / K;           // walkers per warp
-  constexpr int IPW = kTileItems / G;  // items per walker per tile
-  const int lane = threadIdx.x & 31;
-  const int gw = lane / K;  // walker index
-  const int c = lane % K;   // right-hand side handled by this lane
-  const int64_t total = g.n + g.nnz;
-  const int64_t t_begin = wg * g.tiles_per_warp;
-  int64_t t_end = t_begin + g.tiles_per_warp;
-  if (t_end > g.n_tiles) t_end = g.n_tiles;
-  T quad = num<T>(0.f);
-  if (t_begin >= t_end) return quad;
-
-  // tile row coordinates of 32 tiles at a time live in one register per lane
-  int32_t trow = g.tile_row[t_begin + (lane < t_end - t_begin + 1 ? lane : 0)];
-  int64_t tbase = t_begin;
-  int32_t carry_row = __shfl_sync(kFull, trow, 0);
-  T carry = num<T>(0.f);
-  for (int64_t t = t_begin; t < t_end; ++t) {
-    if (t + 1 - tbase >= 32) {  // refill the coordinate window
-      tbase = t;
-      const int64_t q = t + lane;
-      trow = g.tile_row[q <= t_end ? q : t_end];
-    }
-    const int32_t r0 = __shfl_sync(kFull, trow, (int)(t - tbase));
-    const int32_t r1 = __shfl_sync(kFull, trow, (int)(t + 1 - tbase));
-    const int64_t d0 = t * kTileItems;
-    int64_t d1 = d0 + kTileItems;
-    if (d1 > total) d1 = total;
-    const int32_t k0 = (int32_t)(d0 - r0);
-    const int32_t k1 = (int32_t)(d1 - r1);
-    const int32_t rlast = (r1 < g.n - 1) ? r1 : (int32_t)(g.n - 1);
-    const int nre = rlast - r0 + 1;
-    const int nk = k1 - k0;
-    __syncwarp();
-    // Staging in two waves, each issuing all of its global loads before any
-    // shared-memory store (a store between loads would serialise them):
-    // wave 1 row ends, columns and weights; wave 2 the gathers x[col], x[r].
-    constexpr int kPer = (kTileItems + 31) / 32;
-    int32_t cj[kPer];
-    {
-      int32_t rev[kPer + 1];
-      float wv[kPer];
-#pragma unroll
-      for (int u = 0; u <= kPer; ++u) {
-        const int j = lane + 32 * u;
-        rev[u] = (j < nre) ? g.row_ptr[r0 + 1 + j] : 0;
-      }
-#pragma unroll
-      for (int u = 0; u < kPer; ++u) {
-        const int j = lane + 32 * u;
-        cj[u] = (j < nk) ? g.col[k0 + j] : 0;
-        wv[u] = (g.val && j < nk) ? g.val[k0 + j] : 1.0f;
-      }
-#pragma unroll
-      for (int u = 0; u <= kPer; ++u) {
-        const int j = lane + 32 * u;
-        if (j < nre) s_re[j] = rev[u];
-      }
-#pragma unroll
-      for (int u = 0; u < kPer; ++u) {
-        const int j = lane + 32 * u;
-        if (j < nk) {
-          s_val[j] = wv[u];
-          if (!kStageX) sm->col[j] = cj[u];
-        }
-      }
-    }
-    if (kStageX) {
-      T xg[kPer][K];
-      T xrv[kPer + 1];
-#pragma unroll
-      for (int u = 0; u < kPer; ++u) {
-        const int j = lane + 32 * u;
-#pragma unroll
-        for (int cc = 0; cc < K; ++cc) xg[u][cc] = (j < nk) ? x[(int64_t)cj[u] * K + cc] : num<T>(0.f);
-      }
-      // x of the tile's rows: nre * K consecutive values
-#pragma unroll
-      for (int u = 0; u <= kPer; ++u) {
-        const int e = lane + 32 * u;
-        xrv[u] = (e < nre * K) ? x[(int64_t)r0 * K + e] : num<T>(0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < kPer; ++u) {
-        const int j = lane + 32 * u;
-        if (j < nk) {
-#pragma unroll
-          for (int cc = 0; cc < K; ++cc) smx->xj[j * K + cc] = xg[u][cc];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u <= kPer; ++u) {
-        const int e = lane + 32 * u;
-        if (e < nre * K) smx->xr[e] = xrv[u];
-      }
-      // rows beyond 32 * (kPer + 1) / K of a tile (only when K > 1)
-      for (int e = lane + 32 * (kPer + 1); e < nre * K; e += 32) smx->xr[e] = x[(int64_t)r0 * K + e];
-    }
-    __syncwarp();
-
-    const int len = (int)(d1 - d0);
-    int dl = gw * IPW;
-    if (dl > len) dl = len;
-    int de = dl + IPW;
-    if (de > len) de = len;
-    // merge-path split of local diagonal dl inside the tile
-    int lo = dl - nk;
-    if (lo < 0) lo = 0;
-    int hi = r1 - r0;
-    if (hi > dl) hi = dl;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if ((s_re[mid - 1] - k0) + mid <= dl)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    int rl = lo;       // local row
-    int k = dl - lo;   // local nonzero index
-    T xr = num<T>(0.f);
-    T xr_nx = num<T>(0.f);  // wide walks: x of the next row, loaded one row ahead
-    if (MODE == kLap && r0 + rl < g.n)
-      xr = kStageX ? smx->xr[rl * K + c] : x[(int64_t)(r0 + rl) * K + c];
-    if (kPre && r0 + rl + 1 < g.n) xr_nx = x[(int64_t)(r0 + rl + 1) * K + c];
-    T acc = num<T>(0.f);
-    bool femit = false;
-    T fval = num<T>(0.f);
-    const int frl = rl;
-    // Two halves of PD/2 nonzeros: one being read, the next one in flight.
-    constexpr int HB = PD / 2;
-    int cbase = -1;  // local index of the first nonzero of the half being read
-    int cur = 0;     // which half is being read
-    T* wbuf = gbuf + gw * PD * K;
-    auto issue_half = [&](int base, int half) {
-#pragma unroll 4
-      for (int i = 0; i < HB; ++i) {
-        if (base + i < nk) {
-          const T* src = x + (int64_t)sm->col[base + i] * K + c;
-          if constexpr (sizeof(T) == 4)
-            cp_async4(&wbuf[(half * HB + i) * K + c], src);
-          else
-            cp_async8(&wbuf[(half * HB + i) * K + c], src);
-        }
-      }
-      cp_async_commit_group();
-    };
-    for (int it = dl; it < de; ++it) {
-      const int rend = s_re[rl] - k0;
-      if (k < rend) {
-        const float w = g.val ? s_val[k] : 1.0f;
-        if (MODE == kRowSum) {
-          acc += num<T>(w);
-        } else {
-          if (kPre) {  // walker-uniform; each lane reads and copies only its own column
-            if (cbase < 0) {
-              cbase = k;
-              cur = 0;
-              issue_half(k, 0);
-              issue_half(k + HB, 1);
-              cp_async_wait_one();
-            } else if (k >= cbase + HB) {
-              cbase += HB;
-              cur ^= 1;
-              issue_half(cbase + HB, cur ^ 1);
-              cp_async_wait_one();
-            }
-          }
-          const T xj = kStageX ? smx->xj[k * K + c]
-                               : (kPre ? wbuf[(cur * HB + (k - cbase)) * K + c] : x[(int64_t)sm->col[k] * K + c]);
-          const T df = xr - xj;
-          const T tw = mul_w(df, w);
-          acc += tw;
-          quad += tw * df;
-        }
-        ++k;
-      } else {
-        if (!femit) {
-          femit = true;
-          fval = acc;
-        } else {
-          out[(int64_t)(r0 + rl) * K + c] = acc;
-        }
-        acc = num<T>(0.f);
-        ++rl;
-        if (kPre) {
-          xr = xr_nx;
-          if (r0 + rl + 1 < g.n) xr_nx = x[(int64_t)(r0 + rl + 1) * K + c];
-        } else if (MODE == kLap && r0 + rl < g.n) {
-          xr = kStageX ? smx->xr[rl * K + c] : x[(int64_t)(r0 + rl) * K + c];
-        }
-      }
-    }
-    if (kPre && cbase >= 0) cp_async_wait_all();  // the buffer is reused by the next tile
-    int32_t crow = r0 + rl;
-    T cval = acc;
-    if (gw == 0) {
-      if (femit)
-        fval += carry;
-      else
-        cval += carry;
-    }
-    T scan = cval;
-#pragma unroll
-    for (int off = 1; off < G; off <<= 1) {
-      const T v = shfl_up_v(scan, off * K);
-      const int32_t kr = __shfl_up_sync(kFull, crow, off * K);
-      if (gw >= off && kr == crow) scan += v;
-    }
-    const T prev = shfl_up_v(scan, K);
-    if (femit) out[(int64_t)(r0 + frl) * K + c] = fval + (gw > 0 ? prev : num<T>(0.f));
-    carry = shfl_v(scan, (G - 1) * K + c);
-    carry_row = __shfl_sync(kFull, crow, (G - 1) * K + c);
-  }
-  if (lane == 0) wc_row[wg] = carry_row;
-  if (lane < K) wc_val[wg * K + lane] = carry;
-  return quad;
-}
 
 // ------------------------------------------------------------ sliced ELL
 //
@@ -578,6 +243,10 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
 //          row end) and their x values are staged in shared memory first.
 constexpr int kWB = 8;
 
+// Shared memory per warp for the slice rows' own values x_r (32 rows of K
+// values, when they fit).
+constexpr int kWideStageBytes = 4096;
+
 template <typename T, int K>
 __device__ __forceinline__ void wide_unit(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
                                           T* __restrict__ part, int* __restrict__ cnt, int64_t u, T& quad,
@@ -642,7 +311,7 @@ __device__ __forceinline__ void wide_unit(const SellGraph& g, const T* __restric
   // slice: rows [ra, rb) of this sub-group; row i of the slice is owned by
   // sub-group i / RB, whose lanes are [i / RB * K, ...) = the lanes that
   // hold the row ends of its rows (RB == K).
-  constexpr bool kStageXr = 32 * K * (int)sizeof(T) <= kGatherBytesPerWarp;
+  constexpr bool kStageXr = 32 * K * (int)sizeof(T) <= kWideStageBytes;
   const int64_t s = u - g.n_chunks;
   const int64_t rs = g.n_long + 32 * s;
   const int64_t ra = rs + (int64_t)sg * RB;
@@ -709,19 +378,6 @@ __device__ __forceinline__ void wide_unit(const SellGraph& g, const T* __restric
       }
     }
   }
-}
-
-// Adds to `own` (the value written for row i by the warp holding its row
-// end) the carries of the warps whose runs end inside row i, in warp order.
-template <typename T, int K>
-__device__ __forceinline__ T row_total(int64_t i, T own, const int32_t* __restrict__ row_ptr,
-                                       const T* __restrict__ wc_val, const FastDiv& ipw, int c) {
-  const uint32_t a = (uint32_t)i + (uint32_t)row_ptr[i];
-  const uint32_t b = (uint32_t)i + (uint32_t)row_ptr[i + 1];
-  const uint32_t wa = ipw.div(a);
-  const uint32_t wb = ipw.div(b);
-  for (uint32_t w = wa; w < wb; ++w) own += wc_val[(int64_t)w * K + c];
-  return own;
 }
 
 }  // namespace fj
