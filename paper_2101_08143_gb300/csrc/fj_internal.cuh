@@ -31,7 +31,7 @@ constexpr int kPad = 64;
 // Rows with at most kSellMaxLen entries go to sliced ELL; longer rows are
 // processed warp-wide in chunks of at most kChunkLen entries.
 constexpr int kSellMaxLen = 64;
-constexpr int kChunkLen = 2048;
+constexpr int kChunkLen = 512;
 // Degree keys of the reordering sort saturate here (11-bit keys).
 constexpr int kDegKeyMax = 2047;
 

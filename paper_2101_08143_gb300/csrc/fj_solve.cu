@@ -58,7 +58,6 @@ struct SolveParams {
   const int32_t* perm;  // solver node -> input id
   VI* hub_part;         // [n_chunks][K] chunk sums of multi-chunk rows
   df64* hub_part64;
-  int* hub_cnt;         // [n_long] finished chunks per long row
   double* quad_u;       // [n_units][K] edge sums per work unit (K >= 8)
   unsigned long long* unit_counter;  // next work unit of the wide walks
   const float* dinv;
@@ -179,7 +178,7 @@ __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 // not depend on which warp took which unit.
 template <typename T, int K>
 __device__ __forceinline__ void wide_walk(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
-                                          T* __restrict__ part, int* __restrict__ cnt,
+                                          T* __restrict__ part,
                                           unsigned long long* counter, unsigned long long base,
                                           double* __restrict__ quad_u, T* __restrict__ sxr) {
   const int lane = threadIdx.x & 31;
@@ -189,7 +188,7 @@ __device__ __forceinline__ void wide_walk(const SellGraph& g, const T* __restric
     const int64_t u = (int64_t)__shfl_sync(kFull, k, 0);
     if (u >= g.n_units) break;
     T q = num<T>(0.f);
-    wide_unit<T, K>(g, x, out, part, cnt, u, q, sxr);
+    wide_unit<T, K>(g, x, out, part, u, q, sxr);
     double qd = to_double(q);
 #pragma unroll
     for (int off = K; off < 32; off <<= 1) qd += __shfl_xor_sync(kFull, qd, off);
@@ -262,14 +261,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
     u0 = P.sg.n_units * (int64_t)blockIdx.x / gridDim.x;
     u1 = P.sg.n_units * (int64_t)(blockIdx.x + 1) / gridDim.x;
   } else {
+    // range wr of W: consecutive ranges (units of similar kind) go to
+    // different blocks, so that every SM gets a mix of hub chunks and slices
     const int lane = threadIdx.x & 31;
     const int64_t W = (int64_t)gridDim.x * kWarps;
+    const int64_t wr = (int64_t)warp * gridDim.x + blockIdx.x;
     int64_t v = 0;
-    if (lane < 2) v = sell_unit_start(P.sg, wg + lane, W);
+    if (lane < 2) v = sell_unit_start(P.sg, wr + lane, W);
     u0 = __shfl_sync(kFull, v, 0);
     u1 = __shfl_sync(kFull, v, 1);
   }
-  for (int64_t i = gtid; i < P.sg.n_long; i += gstride) P.hub_cnt[i] = 0;
   const unsigned long long unit_step = (unsigned long long)P.sg.n_units + (unsigned long long)gridDim.x * kWarps;
 
   // ---------------------------------------------------------------- setup
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         } else {
           sb = P.sbar[idx];
           qv = P.q[idx];
-          lq = i < P.sg.n_nz ? P.t64[idx] : z0;
+          lq = row_t<df64, K>(P.sg, P.t64, P.hub_part64, i, idx, c);
         }
         const df64 r64 = df_sub(df_sub(sb, qv), lq);
         a_rr64 += df_mul(r64, r64);
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         double qv;
         if constexpr (kSell) {
           if constexpr (kWide) {
-            wide_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.hub_cnt, P.unit_counter, unit_base, P.quad_u, my_sxr);
+            wide_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.unit_counter, unit_base, P.quad_u, my_sxr);
             unit_base += unit_step;
             if (!grid_sync(P.bar, status, epoch)) return;
             qv = unit_sum<K>(P.quad_u, u0, u1);
@@ -427,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
             VI quad[K];
 #pragma unroll
             for (int cc = 0; cc < K; ++cc) quad[cc] = VI(0);
-            sell_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.hub_cnt, u0, u1, quad);
+            sell_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, u0, u1, quad);
             qv = lane_share<VI, K>(quad);
           }
         }
@@ -494,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
             if (idx < NK) {
               const int64_t i = idx / K;
               uv[e] = vu[idx];
-              tv[e] = i < P.sg.n_nz ? vt[idx] : VI(0);
+              tv[e] = row_t<VI, K>(P.sg, vt, P.hub_part, i, idx, c);
               pv[e] = fst ? VI(0) : vp[idx];
               dv[e] = fst ? VI(0) : vd[idx];
               xv[e] = vx[idx];
@@ -572,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       double quad;
       if constexpr (kSell) {
         if constexpr (kWide) {
-          wide_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, P.hub_cnt, P.unit_counter, unit_base, P.quad_u,
+          wide_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, P.unit_counter, unit_base, P.quad_u,
                              my_sxr64);
           unit_base += unit_step;
           if (!grid_sync(P.bar, status, epoch)) return;
@@ -581,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
           df64 qd[K];
 #pragma unroll
           for (int cc = 0; cc < K; ++cc) qd[cc] = df_from_float(0.0f);
-          sell_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, P.hub_cnt, u0, u1, qd);
+          sell_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, u0, u1, qd);
           quad = lane_share<df64, K>(qd);
         }
       }
@@ -666,7 +667,6 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.part = (double*)take((size_t)blocks * NSLOT * K * 8);
   P.hub_part = (VI*)take(std::max<int64_t>(g->n_chunks, 1) * K * sizeof(VI));
   P.hub_part64 = (df64*)take(std::max<int64_t>(g->n_chunks, 1) * K * 8);
-  P.hub_cnt = (int*)take(std::max<int64_t>(g->n_long, 1) * 4);
   P.quad_u = (double*)take(std::max<int64_t>(g->n_units, 1) * K * 8);
   P.bar = (Barrier*)take(64);  // the barrier, then the unit counter
   P.unit_counter = (unsigned long long*)((char*)P.bar + 32);
@@ -703,7 +703,6 @@ size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int n
   add((size_t)blocks * NSLOT * K * 8);
   add(std::max<int64_t>(g->n_chunks, 1) * K * inner_bytes);
   add(std::max<int64_t>(g->n_chunks, 1) * K * 8);
-  add(std::max<int64_t>(g->n_long, 1) * 4);
   add(std::max<int64_t>(g->n_units, 1) * K * 8);
   add(64);
   return b;

@@ -27,11 +27,11 @@ constexpr unsigned kFull = 0xffffffffu;
 // col/val is one coalesced 128-byte line, the K values of x_j come in one
 // vector load, and a row's sum is accumulated by one lane in entry order.
 // Long rows are cut into chunks processed by a whole warp (lanes stride over
-// the chunk, then a fixed xor-tree reduction).  A row with several chunks is
-// finished by the warp that completes its last chunk: chunk sums go to
-// part[], a per-row counter counts finished chunks, and the last finisher
-// adds the row's chunk sums in chunk order.  Every row sum is therefore the
-// same bits whichever warp computes which unit.
+// the chunk, then a fixed xor-tree reduction).  A row of one chunk is
+// written directly; a row of several chunks leaves one partial sum per chunk
+// in part[], and the phase after the walk's barrier adds them in chunk order
+// (row_t).  Every row sum is therefore the same bits whichever warp computes
+// which unit, with no fence or atomic inside the walk.
 
 struct SellGraph {
   const int32_t* row_ptr;  // solver-order CSR (long rows)
@@ -85,10 +85,12 @@ __device__ __forceinline__ void load_k(const T* __restrict__ p, T (&v)[K]) {
   }
 }
 
-// First work unit of warp w of W when units are split by cumulative cost.
+// First work unit of range w of W when units are split by cumulative cost:
+// the unit boundary nearest to w/W of the total (monotone in w, 0 for w = 0,
+// n_units for w = W).
 __device__ __forceinline__ int64_t sell_unit_start(const SellGraph& g, int64_t w, int64_t W) {
   const int64_t total = g.unit_prefix[g.n_units];
-  const int64_t target = (w * total + W - 1) / W;  // ceil(w * total / W)
+  const int64_t target = (w * total + W / 2) / W;  // round(w * total / W)
   int64_t lo = 0, hi = g.n_units;  // first u with prefix[u] >= target
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
@@ -97,6 +99,7 @@ __device__ __forceinline__ int64_t sell_unit_start(const SellGraph& g, int64_t w
     else
       hi = mid;
   }
+  if (lo > 0 && target - g.unit_prefix[lo - 1] < g.unit_prefix[lo] - target) --lo;
   return lo;
 }
 
@@ -104,7 +107,7 @@ __device__ __forceinline__ int64_t sell_unit_start(const SellGraph& g, int64_t w
 // [u0, u1); quad[c] accumulates this lane's share of sum w (x_r - x_j)^2.
 template <typename T, int K>
 __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
-                                          T* __restrict__ part, int* __restrict__ cnt, int64_t u0,
+                                          T* __restrict__ part, int64_t u0,
                                           int64_t u1, T (&quad)[K]) {
   const int lane = threadIdx.x & 31;
   // entries in flight per lane between two dependent round trips
@@ -150,41 +153,10 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
 #pragma unroll
       for (int cc = 1; cc < K; ++cc)
         if (lane == cc) mine = acc[cc];
-      const int32_t f = g.long_first[r];
-      const int32_t nch = g.long_first[r + 1] - f;
-      if (nch == 1) {
-        if (lane < K) out[(int64_t)r * K + lane] = mine;
-      } else {
-        if (lane < K) {
-          part[u * K + lane] = mine;
-          __threadfence();
-        }
-        __syncwarp();
-        int done = 0;
-        if (lane == 0) done = atomicAdd(&cnt[r], 1) == nch - 1;
-        done = __shfl_sync(kFull, done, 0);
-        if (done) {
-          __threadfence();
-          T tot[K];
-#pragma unroll
-          for (int cc = 0; cc < K; ++cc) tot[cc] = num<T>(0.f);
-          for (int32_t q = f + lane; q < f + nch; q += 32) {
-#pragma unroll
-            for (int cc = 0; cc < K; ++cc) tot[cc] += ldcg_v(&part[(int64_t)q * K + cc]);
-          }
-#pragma unroll
-          for (int cc = 0; cc < K; ++cc) {
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) tot[cc] += shfl_xor_v(tot[cc], off);
-          }
-          T t = tot[0];
-#pragma unroll
-          for (int cc = 1; cc < K; ++cc)
-            if (lane == cc) t = tot[cc];
-          if (lane < K) out[(int64_t)r * K + lane] = t;
-          if (lane == 0) cnt[r] = 0;
-        }
-      }
+      // a row of one chunk is final; chunks of longer rows leave partial
+      // sums, which the next phase adds up in chunk order (row_t)
+      const int32_t nch = g.long_first[r + 1] - g.long_first[r];
+      if (lane < K) (nch == 1 ? out[(int64_t)r * K + lane] : part[u * K + lane]) = mine;
     } else {
       const int64_t s = u - g.n_chunks;
       const int64_t off = g.slice_off[s];
@@ -234,8 +206,8 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
 // sub-groups of K lanes; every gathered row x_j is one K-wide coalesced load.
 // Work units are the same as for narrow K (long-row chunks, 32-row slices):
 //   chunk: the sub-groups stride over the chunk's entries, kWB entries per
-//          sub-group in flight, then an xor tree across sub-groups; chunks
-//          of one row are finished as in chunk_walk;
+//          sub-group in flight, then an xor tree across sub-groups; chunk
+//          partials of multi-chunk rows are left for row_t, as for narrow K;
 //   slice: sub-group sg owns the RB = 32/SUB consecutive rows
 //          [rs + sg*RB, rs + (sg+1)*RB); their entries are one contiguous run
 //          of the CSR, summed in batches of kWB entries that run across row
@@ -249,7 +221,7 @@ constexpr int kWideStageBytes = 4096;
 
 template <typename T, int K>
 __device__ __forceinline__ void wide_unit(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
-                                          T* __restrict__ part, int* __restrict__ cnt, int64_t u, T& quad,
+                                          T* __restrict__ part, int64_t u, T& quad,
                                           T* __restrict__ sxr) {
   constexpr int SUB = 32 / K;
   constexpr int RB = 32 / SUB;  // rows per sub-group in a slice
@@ -284,28 +256,8 @@ __device__ __forceinline__ void wide_unit(const SellGraph& g, const T* __restric
     }
 #pragma unroll
     for (int off = K; off < 32; off <<= 1) acc += shfl_xor_v(acc, off);
-    const int32_t f = g.long_first[r];
-    const int32_t nch = g.long_first[r + 1] - f;
-    if (nch == 1) {
-      if (sg == 0) out[(int64_t)r * K + c] = acc;
-      return;
-    }
-    if (sg == 0) {
-      part[u * K + c] = acc;
-      __threadfence();
-    }
-    __syncwarp();
-    int done = 0;
-    if (lane == 0) done = atomicAdd(&cnt[r], 1) == nch - 1;
-    done = __shfl_sync(kFull, done, 0);
-    if (!done) return;
-    __threadfence();
-    T tot = num<T>(0.f);
-    for (int32_t q = f + sg; q < f + nch; q += SUB) tot += ldcg_v(&part[(int64_t)q * K + c]);
-#pragma unroll
-    for (int off = K; off < 32; off <<= 1) tot += shfl_xor_v(tot, off);
-    if (sg == 0) out[(int64_t)r * K + c] = tot;
-    if (lane == 0) cnt[r] = 0;
+    const int32_t nch = g.long_first[r + 1] - g.long_first[r];
+    if (sg == 0) (nch == 1 ? out[(int64_t)r * K + c] : part[u * K + c]) = acc;
     return;
   }
   // slice: rows [ra, rb) of this sub-group; row i of the slice is owned by
@@ -378,6 +330,24 @@ __device__ __forceinline__ void wide_unit(const SellGraph& g, const T* __restric
       }
     }
   }
+}
+
+// Row i of the walk's output: out[i*K+c] as written by the walk, or for a
+// row of several chunks the sum of its chunk partials in chunk order, or 0
+// for a row without entries.  Valid after the barrier that ends the walk.
+template <typename T, int K>
+__device__ __forceinline__ T row_t(const SellGraph& g, const T* __restrict__ out, const T* __restrict__ part,
+                                   int64_t i, int64_t idx, int c) {
+  if (i >= g.n_nz) return num<T>(0.f);
+  if (i < g.n_long) {
+    const int32_t f = g.long_first[i], l = g.long_first[i + 1];
+    if (l - f > 1) {
+      T s = part[(int64_t)f * K + c];
+      for (int32_t q = f + 1; q < l; ++q) s += part[(int64_t)q * K + c];
+      return s;
+    }
+  }
+  return out[idx];
 }
 
 }  // namespace fj
