@@ -66,6 +66,9 @@ enum {
 /* Where a call's pointers live. */
 #define FJ_HOST_PTRS 0u
 #define FJ_DEVICE_PTRS 1u
+/* Upload flag: a pair listed more than once is a set of parallel edges whose
+ * weights add (default: such an edge list is rejected with FJ_ERR_GRAPH). */
+#define FJ_MERGE_DUPLICATES 2u
 
 /* Arithmetic of the solve (fj_opts.precision). */
 enum {
@@ -85,7 +88,8 @@ typedef struct fj_opts {
   int32_t precision;  /* FJ_PREC_* (FJ_PREC_MIXED)                           */
   int32_t max_iter;   /* cap on inner iterations over the whole solve (20000)*/
   int32_t max_refine; /* cap on float64 refinement steps (12)                */
-  uint32_t flags;     /* FJ_HOST_PTRS or FJ_DEVICE_PTRS for s, z             */
+  uint32_t flags;     /* FJ_HOST_PTRS or FJ_DEVICE_PTRS for s, z; for
+                         fj_submit_edges also FJ_MERGE_DUPLICATES          */
 } fj_opts;
 
 typedef struct fj_info {
@@ -145,13 +149,16 @@ fj_status fj_set_max_blocks(fj_ctx* ctx, int32_t max_blocks);
  *   m        number of listed undirected edges (>= 0); each edge once
  *   src,dst  int32[m] endpoints in [0, n) (host or device, see flags)
  *   w        float32[m] weights > 0 and finite, or NULL for unit weights
- *   flags    FJ_HOST_PTRS or FJ_DEVICE_PTRS
- * Self-loops are dropped (b_e = 0 adds nothing to L).  A repeated pair is a
- * parallel edge: its weights add, as in L = sum_e w_e b_e b_e^T.  The graph
- * need not be connected.  2 * m (minus self-loops) must stay below 2^31.
- * The graph lives in device memory until fj_graph_free.
- * Errors: FJ_ERR_ARG, FJ_ERR_GRAPH (bad id or weight; nothing allocated
- * remains), FJ_ERR_OOM, FJ_ERR_CUDA. */
+ *   flags    FJ_HOST_PTRS or FJ_DEVICE_PTRS, optionally | FJ_MERGE_DUPLICATES
+ * Self-loops are dropped (b_e = 0 adds nothing to L).  The graph of Sec. 2.1
+ * is simple: a pair {u, v} listed more than once (in either orientation) is
+ * rejected, unless FJ_MERGE_DUPLICATES is given, in which case the repeats
+ * are parallel edges whose weights add, as in L = sum_e w_e b_e b_e^T.  The
+ * graph need not be connected.  2 * m (minus self-loops) must stay below
+ * 2^31.  The graph lives in device memory until fj_graph_free.
+ * Errors: FJ_ERR_ARG, FJ_ERR_GRAPH (bad id or weight, or a repeated pair
+ * without FJ_MERGE_DUPLICATES; nothing allocated remains), FJ_ERR_OOM,
+ * FJ_ERR_CUDA. */
 fj_status fj_graph_upload(fj_ctx* ctx, int64_t n, int64_t m,
                           const int32_t* src, const int32_t* dst,
                           const float* w, uint32_t flags, fj_graph** out);
@@ -220,7 +227,8 @@ fj_status fj_submit(fj_ctx* ctx, const fj_graph* g, int32_t k,
 /* Queues a request that brings its own graph: an edge list as for
  * fj_graph_upload (HOST pointers, copied before the call returns).  The graph
  * is built on the device when the request is admitted and freed when it
- * finishes; a bad node id or weight is reported by fj_poll (FJ_ERR_GRAPH). */
+ * finishes; a bad node id or weight, or a repeated pair unless opts->flags
+ * has FJ_MERGE_DUPLICATES, is reported by fj_poll (FJ_ERR_GRAPH). */
 fj_status fj_submit_edges(fj_ctx* ctx, int64_t n, int64_t m,
                           const int32_t* src, const int32_t* dst,
                           const float* w, int32_t k, const double* s,

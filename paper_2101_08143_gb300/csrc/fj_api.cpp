@@ -20,7 +20,7 @@
 // defined in fj_graph.cu / fj_solve.cu
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m,
                                 const int32_t* src, const int32_t* dst, const float* w,
-                                fj_graph** out);
+                                bool merge_duplicates, fj_graph** out);
 fj_status fj_free_graph_device(fj_graph* g, cudaStream_t st);
 size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms);
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k,
@@ -268,13 +268,14 @@ fj_status fj_graph_upload(fj_ctx* c, int64_t n, int64_t m, const int32_t* src, c
     set_error("fj_graph_upload: src/dst is NULL");
     return FJ_ERR_ARG;
   }
-  if (flags & ~FJ_DEVICE_PTRS) {
+  if (flags & ~(FJ_DEVICE_PTRS | FJ_MERGE_DUPLICATES)) {
     set_error("fj_graph_upload: unknown flags 0x%x", flags);
     return FJ_ERR_ARG;
   }
   FJ_CUDA(cudaSetDevice(c->device));
+  const bool merge = (flags & FJ_MERGE_DUPLICATES) != 0;
   if (flags & FJ_DEVICE_PTRS)
-    return fj_build_graph_device(c->device, c->stream, n, m, src, dst, w, out);
+    return fj_build_graph_device(c->device, c->stream, n, m, src, dst, w, merge, out);
   // host edge list: copy it to the device first
   int32_t *ds = nullptr, *dd = nullptr;
   float* dw = nullptr;
@@ -295,7 +296,7 @@ fj_status fj_graph_upload(fj_ctx* c, int64_t n, int64_t m, const int32_t* src, c
     if (e == cudaSuccess && w) e = cudaMemcpyAsync(dw, w, m * 4, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "fj_graph_upload copy");
   }
-  if (rc == FJ_OK) rc = fj_build_graph_device(c->device, c->stream, n, m, ds, dd, w ? dw : nullptr, out);
+  if (rc == FJ_OK) rc = fj_build_graph_device(c->device, c->stream, n, m, ds, dd, w ? dw : nullptr, merge, out);
   cudaFreeAsync(ds, c->stream);
   cudaFreeAsync(dd, c->stream);
   if (dw) cudaFreeAsync(dw, c->stream);
@@ -339,7 +340,7 @@ fj_status fj_solve_ex(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, 
   fj_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || o.max_iter < 1 ||
-      o.max_refine < 1 || o.precision < 0 || o.precision > 2 || (o.flags & ~FJ_DEVICE_PTRS)) {
+      o.max_refine < 1 || o.precision < 0 || o.precision > 2 || (o.flags & ~(FJ_DEVICE_PTRS | FJ_MERGE_DUPLICATES))) {
     set_error("fj_solve: invalid options");
     return FJ_ERR_ARG;
   }

@@ -533,6 +533,132 @@ __global__ void k_dinv_weighted(const int32_t* __restrict__ row_ptr, int64_t n, 
   }
 }
 
+// ------------------------------------------------- repeated pairs (Sec. 2.1)
+//
+// Without FJ_MERGE_DUPLICATES the edge list must be simple.  A pair listed
+// twice gives two entries of equal column in both of its rows, so it is
+// found by checking that no row repeats a column.  A hit records the pair's
+// input ids (smaller first; the smallest pair wins) in err[2].
+
+__device__ __forceinline__ void report_duplicate(int64_t* err, const int32_t* perm, int64_t r, int32_t c) {
+  const uint32_t a = (uint32_t)perm[r], b = (uint32_t)perm[c];
+  const unsigned long long pair =
+      ((unsigned long long)(a < b ? a : b) << 32) | (unsigned long long)(a < b ? b : a);
+  atomicOr(reinterpret_cast<unsigned long long*>(&err[0]), (unsigned long long)kErrDuplicate);
+  atomicMin(reinterpret_cast<unsigned long long*>(&err[2]), pair);
+}
+
+// Short rows [n_long, n_nz) (at most kSellMaxLen entries): each warp takes
+// the rows whose first entry falls in its share of the entries, and packs as
+// many whole rows as fit into a window of 32 entries.  One match over the
+// keys (row within the window, column) finds a repeat; a row of 33..64
+// entries compares its two halves, then each of its second-half entries
+// against the first half.
+__global__ void k_dup_short(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const int64_t* __restrict__ cnt, const int32_t* __restrict__ perm,
+                            int64_t* __restrict__ err) {
+  const int64_t n_long = cnt[0], n_nz = cnt[1] > cnt[0] ? cnt[1] : cnt[0];
+  if (n_nz <= n_long) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t e0 = row_ptr[n_long], E = (int64_t)row_ptr[n_nz] - e0;
+  // rows [ra, rb): first row whose start is >= the share's first entry
+  int64_t bound = 0;
+  if (lane < 2) {
+    const int64_t target = e0 + (E * (w + lane)) / W;
+    int64_t lo = n_long, hi = n_nz;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (row_ptr[mid] < target)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    bound = lo;
+  }
+  const int64_t ra = __shfl_sync(kFull, bound, 0), rb = __shfl_sync(kFull, bound, 1);
+  const unsigned long long lane_key = ~0ull - (unsigned long long)lane;  // matches no valid key
+  for (int64_t r = ra; r < rb;) {
+    const int32_t p0 = row_ptr[r];
+    // ends of rows r .. r+31 (clamped to the warp's rows)
+    const int64_t rj = r + 1 + lane;
+    const int32_t end = rj <= rb ? row_ptr[rj] : INT32_MAX;
+    const unsigned fit = __ballot_sync(kFull, end - p0 <= 32);  // whole rows in the window (a prefix)
+    const int q = __popc(fit);
+    if (q > 0) {
+      const int32_t wend = __shfl_sync(kFull, end, q - 1);
+      // bit b set where a row starts at window offset b > 0
+      const unsigned starts =
+          __reduce_or_sync(kFull, (lane < q - 1) ? (1u << (end - p0)) : 0u);
+      const int32_t p = p0 + lane;
+      const bool valid = p < wend;
+      const int rl = __popc(starts & ((2u << lane) - 1u));
+      const int32_t c = valid ? col[p] : 0;
+      const unsigned long long key = valid ? (((unsigned long long)rl << 32) | (uint32_t)c) : lane_key;
+      const unsigned peers = __match_any_sync(kFull, key);
+      if (valid && __popc(peers) > 1 && (peers & ((1u << lane) - 1u)) == 0) report_duplicate(err, perm, r + rl, c);
+      r += q;
+    } else {
+      // one row of 33..64 entries
+      const int32_t d = row_ptr[r + 1] - p0;
+      const int32_t a = col[p0 + lane];
+      const bool hb = lane < d - 32;
+      const int32_t bv = hb ? col[p0 + 32 + lane] : 0;
+      // every lane takes part in both matches (no short-circuit around them)
+      const unsigned pa = __match_any_sync(kFull, (unsigned long long)(uint32_t)a);
+      const unsigned long long kb = hb ? (unsigned long long)(uint32_t)bv : lane_key;
+      const unsigned pb = __match_any_sync(kFull, kb);
+      bool hit_a = __popc(pa) > 1;
+      const bool hit_b = hb && __popc(pb) > 1;
+      for (int j = 0; j < d - 32; ++j) hit_a |= (__shfl_sync(kFull, bv, j) == a);
+      if (hit_a) report_duplicate(err, perm, r, a);
+      if (hit_b) report_duplicate(err, perm, r, bv);
+      r += 1;
+    }
+  }
+}
+
+// Long rows [0, n_long): row r owns the hash segment of 2 * deg(r) slots at
+// 2 * row_ptr[r] (set to -1 first); every entry inserts its column by linear
+// probing from a multiplicative hash.  At most half the slots fill, so a
+// probe ends at an empty slot or at its own column within the segment.
+__global__ void k_dup_fill(int32_t* __restrict__ table, const int32_t* __restrict__ row_ptr,
+                           const int64_t* __restrict__ cnt) {
+  const int64_t total = 2 * (int64_t)row_ptr[cnt[0]];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x)
+    table[i] = -1;
+}
+
+__global__ void k_dup_long(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           const int64_t* __restrict__ cnt, const int32_t* __restrict__ chunk_row,
+                           const int32_t* __restrict__ chunk_begin, const int32_t* __restrict__ chunk_end,
+                           int32_t* __restrict__ table, const int32_t* __restrict__ perm,
+                           int64_t* __restrict__ err) {
+  const int64_t n_chunks = cnt[4];
+  const int lane = threadIdx.x & 31;
+  for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < n_chunks;
+       ch += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t r = chunk_row[ch];
+    const int64_t base = 2 * (int64_t)row_ptr[r];
+    const uint32_t size = 2u * (uint32_t)(row_ptr[r + 1] - row_ptr[r]);
+    for (int32_t p = chunk_begin[ch] + lane; p < chunk_end[ch]; p += 32) {
+      const int32_t c = col[p];
+      uint32_t h = (uint32_t)(((uint64_t)((uint32_t)c * 2654435761u) * size) >> 32);
+      for (uint32_t probe = 0; probe < size; ++probe) {
+        const int32_t prev = atomicCAS(&table[base + h], -1, c);
+        if (prev == -1) break;
+        if (prev == c) {
+          report_duplicate(err, perm, r, c);
+          break;
+        }
+        h = (h + 1 == size) ? 0 : h + 1;
+      }
+    }
+  }
+}
+
 static unsigned grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -646,7 +772,7 @@ void fj_free_graph_arrays(fj_graph* g, cudaStream_t st) {
 // Called by the C ABI (fj_api.cpp).  src/dst/w are device pointers.
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m,
                                 const int32_t* src, const int32_t* dst, const float* w,
-                                fj_graph** out) {
+                                bool merge_duplicates, fj_graph** out) {
   const int64_t N = 2 * m;
   const bool weighted = (w != nullptr);
   Pool pool(st);
@@ -655,12 +781,12 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
     return FJ_ERR_OOM;
   };
   // dcnt: [0] n_long [1] n_nz [2] n_slices [3] nnz [4] n_chunks [5] sliced-ELL
-  // entries [6] validation error bits [7] first invalid edge
-  int64_t* dcnt = pool.get<int64_t>(8);
+  // entries [6] error bits [7] first invalid edge [8] first repeated pair
+  int64_t* dcnt = pool.get<int64_t>(9);
   int32_t* deg = pool.get<int32_t>(n);
   if (pool.failed) return oom();
   FJ_CUDA(cudaMemsetAsync(dcnt, 0, 56, st));
-  FJ_CUDA(cudaMemsetAsync(dcnt + 7, 0xff, 8, st));
+  FJ_CUDA(cudaMemsetAsync(dcnt + 7, 0xff, 16, st));
   FJ_CUDA(cudaMemsetAsync(deg, 0, n * sizeof(int32_t), st));
 
   // ---- 1. validation and degrees
@@ -791,14 +917,34 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   }
   if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
 
+  // ---- 6. repeated pairs
+  if (!merge_duplicates && N > 0) {
+    int32_t* table = pool.get<int32_t>(2 * N);
+    if (!table) return fail(oom());
+    count_launches(3);
+    k_dup_fill<<<grid_for(2 * N, 256), 256, 0, st>>>(table, g->row_ptr, dcnt);
+    k_dup_long<<<grid_for(nc_cap * 32, 256), 256, 0, st>>>(g->row_ptr, g->col, dcnt, g->chunk_row,
+                                                           g->chunk_begin, g->chunk_end, table, g->perm,
+                                                           dcnt + 6);
+    k_dup_short<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, g->col, dcnt, g->perm, dcnt + 6);
+    if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
+  }
+
   // ---- sizes and the validation result back to the host (one round trip)
-  int64_t hc[8];
+  int64_t hc[9];
   if (cudaMemcpyAsync(hc, dcnt, sizeof(hc), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return fail(FJ_ERR_CUDA);
-  if (hc[6]) {
+  if (hc[6] & (kErrBadId | kErrBadWeight)) {
     set_error("fj_graph_upload: edge %llu has %s", (unsigned long long)hc[7],
               (hc[6] & kErrBadId) ? "a node id outside [0, n)" : "a weight that is not finite and > 0");
+    return fail(FJ_ERR_GRAPH);
+  }
+  if (hc[6] & kErrDuplicate) {
+    const unsigned long long pr = (unsigned long long)hc[8];
+    set_error("fj_graph_upload: the pair (%u, %u) is listed more than once (FJ_MERGE_DUPLICATES adds the "
+              "weights of repeated pairs)",
+              (unsigned)(pr >> 32), (unsigned)(pr & 0xffffffffu));
     return fail(FJ_ERR_GRAPH);
   }
   g->n_long = hc[0];

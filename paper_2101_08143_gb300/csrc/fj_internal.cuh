@@ -42,6 +42,7 @@ enum : int {
   kErrTimeout = 4,
   kErrNumeric = 8,
   kErrNotConverged = 16,
+  kErrDuplicate = 32,
 };
 
 struct Barrier {

@@ -29,7 +29,7 @@
 #include "fj_internal.cuh"
 
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m, const int32_t* src,
-                                const int32_t* dst, const float* w, fj_graph** out);
+                                const int32_t* dst, const float* w, bool merge_duplicates, fj_graph** out);
 void fj_free_graph_arrays(fj_graph* g, cudaStream_t st);
 size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms);
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k, const double* s, double* z,
@@ -151,7 +151,8 @@ fj_status start(Server& S, Request* r) {
       if (r->weighted) cudaMemcpyAsync(dw, r->w.data(), r->m * 4, cudaMemcpyHostToDevice, st);
     }
     fj_graph* og = nullptr;
-    fj_status rc = fj_build_graph_device(S.device, st, r->n, r->m, ds, dd, r->weighted ? dw : nullptr, &og);
+    fj_status rc = fj_build_graph_device(S.device, st, r->n, r->m, ds, dd, r->weighted ? dw : nullptr,
+                                         (r->opts.flags & FJ_MERGE_DUPLICATES) != 0, &og);
     cudaFreeAsync(ds, st);
     cudaFreeAsync(dd, st);
     if (dw) cudaFreeAsync(dw, st);

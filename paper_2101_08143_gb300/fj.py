@@ -28,6 +28,7 @@ FJ_ERR_TICKET = -9
 
 FJ_HOST_PTRS = 0
 FJ_DEVICE_PTRS = 1
+FJ_MERGE_DUPLICATES = 2
 
 PREC_MIXED = 0
 PREC_FP64 = 1
@@ -189,9 +190,10 @@ class Context:
         _check(load().fj_set_max_blocks(self.handle, int(nblocks)), "fj_set_max_blocks")
 
     # ------------------------------------------------------------- graphs
-    def upload(self, n, src, dst, w=None) -> Graph:
+    def upload(self, n, src, dst, w=None, merge_duplicates=False) -> Graph:
         """Edge list -> device CSR.  numpy arrays (host) or torch CUDA tensors
-        (device); w=None means unit weights."""
+        (device); w=None means unit weights.  A pair listed twice raises
+        FjError unless merge_duplicates, which adds the repeats' weights."""
         h = _P()
         if _is_torch_cuda(src):
             m = int(src.numel())
@@ -206,15 +208,17 @@ class Context:
             keep = (src, dst, w)
             args = (src.ctypes.data, dst.ctypes.data, None if w is None else w.ctypes.data)
             flags = FJ_HOST_PTRS
+        if merge_duplicates:
+            flags |= FJ_MERGE_DUPLICATES
         rc = load().fj_graph_upload(self.handle, int(n), m, _P(args[0]), _P(args[1]),
                                     _P(args[2]), flags, ctypes.byref(h))
         del keep
         _check(rc, "fj_graph_upload")
         return Graph(self, h)
 
-    def upload_edges(self, edges) -> Graph:
+    def upload_edges(self, edges, merge_duplicates=False) -> Graph:
         """Upload a synth.EdgeList."""
-        return self.upload(edges.n, edges.src, edges.dst, edges.w)
+        return self.upload(edges.n, edges.src, edges.dst, edges.w, merge_duplicates)
 
     # -------------------------------------------------------------- solve
     def solve(self, graph: Graph, s, want_z=True, want_quant=True, opts: Opts | None = None,
@@ -323,14 +327,18 @@ def submit(ctx: "Context", graph: "Graph", s, opts: Opts | None = None) -> Ticke
     return Ticket(t.value, k)
 
 
-def submit_edges(ctx: "Context", n, src, dst, w, s, opts: Opts | None = None) -> Ticket:
-    """Queue a request that carries its own edge list (host arrays)."""
+def submit_edges(ctx: "Context", n, src, dst, w, s, opts: Opts | None = None,
+                 merge_duplicates=False) -> Ticket:
+    """Queue a request that carries its own edge list (host arrays); a pair
+    listed twice fails the request unless merge_duplicates."""
     src = np.ascontiguousarray(src, dtype=np.int32)
     dst = np.ascontiguousarray(dst, dtype=np.int32)
     w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
     s2, k = _host_s(s, n)
     t = ctypes.c_uint64()
     o = _serve_opts(opts)
+    if merge_duplicates:
+        o.flags |= FJ_MERGE_DUPLICATES
     _check(load().fj_submit_edges(ctx.handle, int(n), int(src.shape[0]), _P(src.ctypes.data),
                                   _P(dst.ctypes.data), _P(None if w is None else w.ctypes.data), k,
                                   _P(s2.ctypes.data), ctypes.byref(o), ctypes.byref(t)),

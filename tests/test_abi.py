@@ -32,6 +32,14 @@ def test_header_symbols_exported():
     assert not missing, missing
 
 
+def test_header_constants_match_the_binding():
+    text = open(os.path.join(ROOT, "include", "fj.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (FJ_[A-Z_]+) (\d+)u", text)}
+    assert defs["FJ_HOST_PTRS"] == fj.FJ_HOST_PTRS
+    assert defs["FJ_DEVICE_PTRS"] == fj.FJ_DEVICE_PTRS
+    assert defs["FJ_MERGE_DUPLICATES"] == fj.FJ_MERGE_DUPLICATES
+
+
 def test_version_and_defaults():
     assert "sm_103a" in fj.version()
     o = fj.default_opts()

@@ -186,16 +186,54 @@ def test_constant_opinions(ctx):
 
 
 def test_self_loops_and_parallel_edges(ctx):
-    """Self-loops vanish, repeated pairs add their weights."""
+    """Self-loops vanish; with FJ_MERGE_DUPLICATES repeated pairs add their
+    weights, without it they are rejected."""
+    from paper_2101_08143_gb300 import fj
     src = np.array([0, 1, 0, 2, 2, 3, 3], np.int32)
     dst = np.array([1, 2, 1, 2, 3, 3, 0], np.int32)
     w = np.array([0.5, 1.0, 0.25, 9.0, 2.0, 4.0, 0.125], np.float32)
     s = np.array([0.9, 0.1, 0.4, 0.7])
     expect = fo.solve_dense(4, src, dst, w, s)
-    with ctx.upload(4, src, dst, w) as dg:
+    with ctx.upload(4, src, dst, w, merge_duplicates=True) as dg:
         assert dg.stats()["nnz"] == 10
         z, _, _ = ctx.solve(dg, s)
     np.testing.assert_allclose(z, expect, atol=1e-12)
+    with pytest.raises(fj.FJError) as e:
+        ctx.upload(4, src, dst, w)
+    assert e.value.code == fj.FJ_ERR_GRAPH and "(0, 1)" in str(e.value)
+    # self-loops alone are not repeats
+    with ctx.upload(4, src[[1, 3, 4, 5, 6]], dst[[1, 3, 4, 5, 6]], w[[1, 3, 4, 5, 6]]) as dg:
+        assert dg.stats()["nnz"] == 6
+
+
+@pytest.mark.parametrize("hub", [False, True])
+def test_repeated_pair_found_in_short_and_long_rows(ctx, hub):
+    """A pair listed a second time, reversed, is reported with its input ids,
+    both when its rows are short (sliced ELL) and when one of them is a hub
+    row of several chunks."""
+    from paper_2101_08143_gb300 import fj
+    g = synth.chung_lu(20_000, 100_000, 2.1, seed=12, weighted=True)
+    deg = np.bincount(g.src, minlength=g.n) + np.bincount(g.dst, minlength=g.n)
+    if hub:
+        u = int(np.argmax(deg))
+        e = int(np.nonzero((g.src == u) | (g.dst == u))[0][len(g.src) // 7 % int(deg[u])])
+        assert deg[u] > 1024
+    else:
+        e = int(np.nonzero((deg[g.src] <= 64) & (deg[g.dst] <= 64))[0][0])
+    a, b = int(g.src[e]), int(g.dst[e])
+    src = np.append(g.src, b).astype(np.int32)
+    dst = np.append(g.dst, a).astype(np.int32)
+    w = np.append(g.w, np.float32(0.5))
+    with pytest.raises(fj.FJError) as err:
+        ctx.upload(g.n, src, dst, w)
+    assert err.value.code == fj.FJ_ERR_GRAPH
+    assert f"({min(a, b)}, {max(a, b)})" in str(err.value)
+    # merged: the pair's weight is the sum
+    s = synth.opinions_uniform(g.n, 1, 3)[:, 0]
+    zo = fo.solve(g.n, src, dst, w, s)
+    with ctx.upload(g.n, src, dst, w, merge_duplicates=True) as dg:
+        z, _, _ = ctx.solve(dg, s)
+    np.testing.assert_allclose(z, zo, atol=1e-8)
 
 
 def test_disconnected_components(ctx):

@@ -87,6 +87,12 @@ def test_serving_errors(ctx):
     assert rc == fj.FJ_ERR_GRAPH
     # a collected ticket is gone
     assert fj.poll(ctx, t, 0)[0] == fj.FJ_ERR_TICKET
+    # a repeated pair fails the request unless merged
+    src, dst = np.array([0, 1, 1]), np.array([1, 2, 0])
+    t = fj.submit_edges(ctx, 3, src, dst, None, np.array([0.2, 0.5, 0.9]))
+    assert fj.poll(ctx, t, -1)[0] == fj.FJ_ERR_GRAPH
+    t = fj.submit_edges(ctx, 3, src, dst, None, np.array([0.2, 0.5, 0.9]), merge_duplicates=True)
+    assert fj.poll(ctx, t, -1)[0] == fj.FJ_OK
     # a request larger than the whole budget is refused at submit
     fj.serve_config(ctx, mem_budget_bytes=1 << 20)
     g = synth.erdos_renyi(50_000, 200_000, seed=3)
