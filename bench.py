@@ -169,7 +169,9 @@ def aggregate(local_ms, units_per_rank, dist=None, device=None):
 def precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush, reps=5):
     """Solve-only throughput on the resident bench graph, all modes to the
     same relative residual: plain float64 PCG (one opinion vector), mixed
-    precision (one vector) and mixed precision with 32 vectors per call."""
+    precision (one vector), mixed precision with 32 vectors per call, and
+    Algorithm 1 as printed (two solves per vector, FJ_TWO_SOLVES).  Rates
+    count opinion vectors."""
     out = {}
     rng = np.random.default_rng(17)
     dev = src_d.device
@@ -177,9 +179,10 @@ def precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush, reps=
     s1 = s32[:1].contiguous()
     with torch.cuda.stream(stream):
         gr = ctx.upload(g.n, src_d, dst_d, w_d, merge_duplicates=MERGE)
-        for name, prec, sv in (("fp64_k1", fj.PREC_FP64, s1), ("mixed_k1", fj.PREC_MIXED, s1),
-                               ("mixed_k32", fj.PREC_MIXED, s32)):
-            o = fj.default_opts(tol=TOL, precision=prec)
+        for name, prec, sv, flags in (("fp64_k1", fj.PREC_FP64, s1, 0), ("mixed_k1", fj.PREC_MIXED, s1, 0),
+                                      ("mixed_k32", fj.PREC_MIXED, s32, 0),
+                                      ("two_solves_k1", fj.PREC_MIXED, s1, fj.FJ_TWO_SOLVES)):
+            o = fj.default_opts(tol=TOL, precision=prec, flags=flags)
             ctx.solve(gr, sv, opts=o, want_z=False)
             ms, res = [], 0.0
             for _ in range(reps):

@@ -69,6 +69,13 @@ enum {
 /* Upload flag: a pair listed more than once is a set of parallel edges whose
  * weights add (default: such an edge list is rejected with FJ_ERR_GRAPH). */
 #define FJ_MERGE_DUPLICATES 2u
+/* Solve option (fj_opts.flags, fj_solve_ex / fj_solve / fj_quantities only):
+ * Algorithm 1 as printed, with two solves per opinion vector,
+ * z~ = (I + L)^-1 s and q = (I + L)^-1 s_bar, and the quantities
+ * C_I = ||L z~||^2, D = ||W^1/2 B q||^2, P = ||q||^2, C = ||z~||^2,
+ * I_dc = D + C.  z is z~.  The default (one centred solve, z = q + mu 1)
+ * gives the same values in exact arithmetic at half the work. */
+#define FJ_TWO_SOLVES 4u
 
 /* Arithmetic of the solve (fj_opts.precision). */
 enum {
@@ -89,7 +96,8 @@ typedef struct fj_opts {
   int32_t max_iter;   /* cap on inner iterations over the whole solve (20000)*/
   int32_t max_refine; /* cap on float64 refinement steps (12)                */
   uint32_t flags;     /* FJ_HOST_PTRS or FJ_DEVICE_PTRS for s, z; for
-                         fj_submit_edges also FJ_MERGE_DUPLICATES          */
+                         fj_submit_edges also FJ_MERGE_DUPLICATES; for
+                         fj_solve_ex also FJ_TWO_SOLVES                     */
 } fj_opts;
 
 typedef struct fj_info {

@@ -140,15 +140,16 @@ fj_status grow(void** p, size_t* have, size_t need) {
   return FJ_OK;
 }
 
-int decomposition(int32_t k, int* Ks) {
-  int cnt = 0, col = 0;
-  while (col < k) {
+// Launch widths for k columns: 32 at a time, then 16, 8, 4, 2, 1.
+std::vector<int> decomposition(int64_t k) {
+  std::vector<int> Ks;
+  for (int64_t col = 0; col < k;) {
     int K = 32;
     while (K > k - col) K >>= 1;
-    Ks[cnt++] = K;
+    Ks.push_back(K);
     col += K;
   }
-  return cnt;
+  return Ks;
 }
 
 fj_status status_from_bits(int bits) {
@@ -340,26 +341,29 @@ fj_status fj_solve_ex(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, 
   fj_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || o.max_iter < 1 ||
-      o.max_refine < 1 || o.precision < 0 || o.precision > 2 || (o.flags & ~(FJ_DEVICE_PTRS | FJ_MERGE_DUPLICATES))) {
+      o.max_refine < 1 || o.precision < 0 || o.precision > 2 ||
+      (o.flags & ~(FJ_DEVICE_PTRS | FJ_MERGE_DUPLICATES | FJ_TWO_SOLVES))) {
     set_error("fj_solve: invalid options");
     return FJ_ERR_ARG;
   }
   FJ_CUDA(cudaSetDevice(c->device));
   const int64_t n = g->n;
-  int Ks[64];
-  const int launches = decomposition(k, Ks);
+  // two-solve mode runs 2k launch columns (s_j as is, s_j centred)
+  const bool paper = (o.flags & FJ_TWO_SOLVES) != 0;
+  const int64_t cols = paper ? 2 * (int64_t)k : k;
+  const std::vector<int> Ks = decomposition(cols);
+  const int launches = (int)Ks.size();
   const int inner_bytes = o.precision == FJ_PREC_FP64 ? 8 : 4;
   size_t need = 0;
-  for (int i = 0; i < launches; ++i)
-    need = std::max(need, fj_solve_workspace_bytes(g, Ks[i], inner_bytes, c->num_sms));
+  for (int K : Ks) need = std::max(need, fj_solve_workspace_bytes(g, K, inner_bytes, c->num_sms));
   fj_status rc = grow((void**)&c->ws, &c->ws_bytes, need);
   if (rc != FJ_OK) return rc;
-  const size_t small_need = (size_t)k * 5 * 8 + (size_t)k * 8 + (size_t)launches * 3 * 4 + 1024;
+  const size_t small_need = (size_t)cols * 5 * 8 + (size_t)cols * 8 + (size_t)launches * 3 * 4 + 1024;
   rc = grow((void**)&c->small, &c->small_bytes, small_need);
   if (rc != FJ_OK) return rc;
   double* dq = (double*)c->small;
-  double* dres = dq + (size_t)k * 5;
-  int* dstat = (int*)(dres + k);
+  double* dres = dq + (size_t)cols * 5;
+  int* dstat = (int*)(dres + cols);
 
   const bool host = !(o.flags & FJ_DEVICE_PTRS);
   const double* sd = s;
@@ -383,7 +387,7 @@ fj_status fj_solve_ex(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, 
                        &done_launches, c->max_blocks);
   if (rc != FJ_OK) return rc;
   FJ_CUDA(cudaEventRecord(c->ev1, c->stream));
-  std::vector<double> hq((size_t)k * 5), hres(k);
+  std::vector<double> hq((size_t)cols * 5), hres(cols);
   std::vector<int> hstat((size_t)launches * 3);
   FJ_CUDA(cudaMemcpyAsync(hq.data(), dq, hq.size() * 8, cudaMemcpyDeviceToHost, c->stream));
   FJ_CUDA(cudaMemcpyAsync(hres.data(), dres, hres.size() * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -397,8 +401,21 @@ fj_status fj_solve_ex(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, 
     refines = std::max(refines, hstat[3 * i + 2]);
   }
   double worst = 0.0;
-  for (int j = 0; j < k; ++j) worst = std::max(worst, hres[j]);
-  if (quant) memcpy(quant, hq.data(), hq.size() * 8);
+  for (int64_t j = 0; j < cols; ++j) worst = std::max(worst, hres[j]);
+  if (quant && !paper) memcpy(quant, hq.data(), hq.size() * 8);
+  if (quant && paper) {
+    // Algorithm 1: C_I = ||L z~||^2 and C = ||z~||^2 from the column solved
+    // as is, D = ||W^1/2 B q||^2 and P = ||q||^2 from the centred one
+    for (int64_t j = 0; j < k; ++j) {
+      const double* a = &hq[(size_t)(2 * j) * 5];
+      const double* b = &hq[(size_t)(2 * j + 1) * 5];
+      quant[j].C_I = a[0];
+      quant[j].D = b[1];
+      quant[j].P = b[2];
+      quant[j].C = a[3];
+      quant[j].I_dc = b[1] + a[3];
+    }
+  }
   rc = status_from_bits(bits);
   if (info) {
     float ms = 0.f;
@@ -450,8 +467,8 @@ static fj_status check_serve_args(int32_t k, const double* s, const fj_opts* opt
   fj_default_opts(o);
   if (opts) *o = *opts;
   if (!(o->tol > 0.0) || !(o->inner_tol > 0.0) || o->inner_tol >= 1.0 || o->max_iter < 1 || o->max_refine < 1 ||
-      o->precision < 0 || o->precision > 2) {
-    set_error("fj_submit: invalid options");
+      o->precision < 0 || o->precision > 2 || (o->flags & FJ_TWO_SOLVES)) {
+    set_error("fj_submit: invalid options (FJ_TWO_SOLVES is for fj_solve_ex)");
     return FJ_ERR_ARG;
   }
   return FJ_OK;

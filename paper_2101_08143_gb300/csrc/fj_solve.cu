@@ -86,6 +86,10 @@ struct SolveParams {
   int max_iter;
   int max_refine;
   int mode;
+  // two-solve mode (Algorithm 1 as printed): launch columns come in pairs
+  // (2j: s_j solved as is, 2j+1: s_j centred), source column = c >> col_shift
+  int paper;
+  int col_shift;
 };
 
 // Grid-wide barrier with a bounded wait.  The counter only grows: barrier
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   // ---------------------------------------------------------------- setup
   {
     double acc = 0.0;
-    for (int64_t idx = gtid; idx < NK; idx += gstride) acc += P.s[(int64_t)c * P.ld + idx / K];
+    for (int64_t idx = gtid; idx < NK; idx += gstride) acc += P.s[(int64_t)(c >> P.col_shift) * P.ld + idx / K];
     const double v[1] = {acc};
     const int sl[1] = {S_SUM};
     block_store<K, 1>(v, sl, P.part, red);
@@ -286,7 +290,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
     const int sl[1] = {S_SUM};
     grid_reduce<K, 1>(sl, P.part, res);
     if (threadIdx.x < K) {
-      mu[threadIdx.x] = res[S_SUM * K + threadIdx.x] / (double)n;
+      // a column solved as is (two-solve mode, even columns) keeps mu = 0
+      mu[threadIdx.x] = (P.paper && !(threadIdx.x & 1)) ? 0.0 : res[S_SUM * K + threadIdx.x] / (double)n;
       done[threadIdx.x] = 0;
     }
     __syncthreads();
@@ -305,11 +310,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       double a_bb = 0, a_gam = 0, a_rr = 0, a_uu = 0;
       const double m = mu[c];
       const df64 mdf = df_from_double(m);
+      const bool lz_col = P.paper && !(c & 1);
       for (int64_t idx = gtid; idx < NK; idx += gstride) {
         const int64_t i = idx / K;
         df64 sb, qv, lq;
         if (init) {
-          const double sbd = P.s[(int64_t)c * P.ld + P.perm[i]] - m;
+          const double sbd = P.s[(int64_t)(c >> P.col_shift) * P.ld + P.perm[i]] - m;
           sb = df_from_double(sbd);
           P.sbar[idx] = sb;
           P.q[idx] = z0;
@@ -326,7 +332,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         a_p += df_mul(qv, qv);
         const df64 zq = df_add(qv, mdf);
         a_c += df_mul(zq, zq);
-        const df64 dq = df_sub(sb, qv);
+        // C_I = ||s_bar - q||^2, or ||L z~||^2 for a column solved as is
+        // in two-solve mode (lq = off-diagonal part of (I + L) q = L q)
+        const df64 dq = lz_col ? lq : df_sub(sb, qv);
         a_ci += df_mul(dq, dq);
         const VI rv = (VI)r64.hi + (VI)r64.lo;
         const VI uv = P.dinv[i] * rv;
@@ -594,9 +602,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   }
 
   // ---------------------------------------------------------------- output
-  if (P.z_out) {
+  if (P.z_out && !(P.paper && (c & 1))) {
     for (int64_t idx = gtid; idx < NK; idx += gstride)
-      P.z_out[(int64_t)c * P.ld + P.perm[idx / K]] = df_to_double(P.q[idx]) + mu[c];
+      P.z_out[(int64_t)(c >> P.col_shift) * P.ld + P.perm[idx / K]] = df_to_double(P.q[idx]) + mu[c];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     int all_done = 1;
@@ -612,7 +620,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
 template <typename VI, int K>
 static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, const double* s,
                             int64_t ld, double* z, double* quant, double* resid, int* status,
-                            char* ws, size_t ws_bytes, const fj_opts& o, int mode, int max_blocks) {
+                            char* ws, size_t ws_bytes, const fj_opts& o, int mode, int max_blocks,
+                            bool paper) {
   auto kern = k_solve<VI, K>;
   const size_t red_bytes = (size_t)7 * kWarps * K * sizeof(double);
   const size_t stage = (K <= 4) ? 0 : (size_t)kWarps * kWideStageBytes;
@@ -679,6 +688,8 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.max_iter = o.max_iter;
   P.max_refine = o.max_refine;
   P.mode = mode;
+  P.paper = paper ? 1 : 0;
+  P.col_shift = paper ? 1 : 0;
   FJ_CUDA(cudaMemsetAsync(P.bar, 0, 64, st));
   void* args[] = {&P};
   FJ_CUDA(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(kThreads), args, dyn, st));
@@ -716,13 +727,18 @@ fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32
                           char* ws, size_t ws_bytes, const fj_opts& o, int* launches_out,
                           int max_blocks) {
   int mode = o.precision == FJ_PREC_FP64 ? kModeFP64 : (o.precision == FJ_PREC_FP32 ? kModeFP32 : kModeMixed);
+  // two-solve mode: 2k launch columns (s_j as is, s_j centred), quant and
+  // resid per launch column; every launch starts at an even column
+  const bool paper = (o.flags & FJ_TWO_SOLVES) != 0;
+  const int cols = paper ? 2 * k : k;
   int col = 0, li = 0;
-  while (col < k) {
-    const int left = k - col;
+  while (col < cols) {
+    const int left = cols - col;
     int K = 32;
     while (K > left) K >>= 1;
-    const double* sc = s + (int64_t)col * g->n;
-    double* zc = z ? z + (int64_t)col * g->n : nullptr;
+    const int64_t src_col = paper ? col / 2 : col;
+    const double* sc = s + src_col * g->n;
+    double* zc = z ? z + src_col * g->n : nullptr;
     double* qc = quant + (int64_t)col * 5;
     double* rc = resid + col;
     int* stc = status + 3 * li;
@@ -730,10 +746,10 @@ fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32
 #define FJ_LAUNCH(KK)                                                                                  \
   if (mode == kModeFP64)                                                                               \
     rcode = launch_one<double, KK>(g, st, num_sms, sc, g->n, zc, qc, rc, stc, ws, ws_bytes, o, mode,   \
-                                   max_blocks);                                                        \
+                                   max_blocks, paper);                                                 \
   else                                                                                                 \
     rcode = launch_one<float, KK>(g, st, num_sms, sc, g->n, zc, qc, rc, stc, ws, ws_bytes, o, mode,    \
-                                  max_blocks);
+                                  max_blocks, paper);
     switch (K) {
       case 32: FJ_LAUNCH(32) break;
       case 16: FJ_LAUNCH(16) break;
@@ -802,8 +818,8 @@ extern "C" fj_status fj_solve_fixed(const fj_graph* g, void* stream, int32_t k, 
   fj_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || o.max_iter < 1 ||
-      o.max_refine < 1 || o.precision < 0 || o.precision > 2) {
-    set_error("fj_solve_fixed: invalid options");
+      o.max_refine < 1 || o.precision < 0 || o.precision > 2 || (o.flags & FJ_TWO_SOLVES)) {
+    set_error("fj_solve_fixed: invalid options (FJ_TWO_SOLVES is for fj_solve_ex)");
     return FJ_ERR_ARG;
   }
   FJ_CUDA(cudaSetDevice(g->device));

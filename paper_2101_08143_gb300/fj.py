@@ -29,6 +29,7 @@ FJ_ERR_TICKET = -9
 FJ_HOST_PTRS = 0
 FJ_DEVICE_PTRS = 1
 FJ_MERGE_DUPLICATES = 2
+FJ_TWO_SOLVES = 4
 
 PREC_MIXED = 0
 PREC_FP64 = 1
@@ -247,7 +248,7 @@ class Context:
             if want_z:
                 z = z_out if z_out is not None else torch.empty_like(s)
             sp, zp = s.data_ptr(), (z.data_ptr() if z is not None else None)
-            o.flags = FJ_DEVICE_PTRS
+            o.flags = (o.flags & ~FJ_DEVICE_PTRS) | FJ_DEVICE_PTRS
             keep = None
         else:
             s = np.asarray(s, dtype=np.float64)
@@ -265,7 +266,7 @@ class Context:
                     z = np.empty((n, k), dtype=np.float64, order="F")
             sp = sf.ctypes.data
             zp = z.ctypes.data if z is not None else None
-            o.flags = FJ_HOST_PTRS
+            o.flags = (o.flags & ~FJ_DEVICE_PTRS) | FJ_HOST_PTRS
             keep = sf
         quant = (Quant * k)() if want_quant else None
         info = Info()
@@ -307,7 +308,8 @@ def _serve_opts(opts):
     o = Opts()
     load().fj_default_opts(ctypes.byref(o))
     if opts is not None:
-        o = Opts(opts.tol, opts.inner_tol, opts.precision, opts.max_iter, opts.max_refine, 0)
+        o = Opts(opts.tol, opts.inner_tol, opts.precision, opts.max_iter, opts.max_refine,
+                 opts.flags & ~FJ_DEVICE_PTRS)
     return o
 
 

@@ -38,6 +38,7 @@ def test_header_constants_match_the_binding():
     assert defs["FJ_HOST_PTRS"] == fj.FJ_HOST_PTRS
     assert defs["FJ_DEVICE_PTRS"] == fj.FJ_DEVICE_PTRS
     assert defs["FJ_MERGE_DUPLICATES"] == fj.FJ_MERGE_DUPLICATES
+    assert defs["FJ_TWO_SOLVES"] == fj.FJ_TWO_SOLVES
 
 
 def test_version_and_defaults():

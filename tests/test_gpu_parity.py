@@ -157,6 +157,38 @@ def test_deterministic_bits(ctx, k):
     assert q1 == q2 == q3
 
 
+@pytest.mark.parametrize("k,prec", [(1, 0), (3, 0), (17, 0), (2, 1)])
+def test_two_solves_mode_matches_algorithm_1(ctx, k, prec):
+    """FJ_TWO_SOLVES runs Algorithm 1 as printed (z~ from s, q from s_bar;
+    C_I = ||L z~||^2, D = ||W^1/2 B q||^2, P = ||q||^2, C = ||z~||^2) and
+    matches the oracle's step-by-step Algorithm 1 and the definitions."""
+    from paper_2101_08143_gb300 import fj
+    g = synth.chung_lu(8000, 40_000, 2.3, seed=21, weighted=True)
+    s = synth.opinions_batch_mix(g.n, k, 7)
+    zo, qo = _oracle(g, s)
+    o = fj.default_opts(tol=1e-10, precision=prec, flags=fj.FJ_TWO_SOLVES)
+    with ctx.upload_edges(g) as dg:
+        z, q, info = ctx.solve(dg, s, opts=o)
+        _, q1, _ = ctx.solve(dg, s, opts=fj.default_opts(tol=1e-10, precision=prec))
+    assert info["rel_residual"] <= 1e-10
+    for j in range(k):
+        lit = fo.approxim(g.n, g.src, g.dst, g.w, s[:, j])
+        _check_quantities(q[j], lit, s[:, j], 1e-6)
+        _check_quantities(q[j], qo[j], s[:, j], 1e-6)
+        _check_quantities(q[j], q1[j], s[:, j], 1e-6)
+        assert q[j]["I_dc"] == pytest.approx(q[j]["D"] + q[j]["C"], rel=1e-15)
+    np.testing.assert_allclose(z, zo, atol=1e-8)
+
+
+def test_two_solves_mode_rejected_where_unsupported(ctx):
+    from paper_2101_08143_gb300 import fj
+    g = synth.erdos_renyi(500, 2000, seed=4)
+    o = fj.default_opts(flags=fj.FJ_TWO_SOLVES)
+    with pytest.raises(fj.FJError) as e:
+        fj.submit_edges(ctx, g.n, g.src, g.dst, None, np.ones(g.n), opts=o)
+    assert e.value.code == fj.FJ_ERR_ARG
+
+
 # ------------------------------------------------------------ edge cases
 
 def test_edgeless_graph(ctx):
