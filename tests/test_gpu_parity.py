@@ -180,6 +180,26 @@ def test_two_solves_mode_matches_algorithm_1(ctx, k, prec):
     np.testing.assert_allclose(z, zo, atol=1e-8)
 
 
+@pytest.mark.parametrize("dist", ["uniform", "exponential", "power_law"])
+@pytest.mark.parametrize("two", [False, True])
+def test_paper_opinion_distributions(ctx, dist, two):
+    """The paper's three opinion distributions (uniform, exponential and
+    power law with exponent 2.5, each scaled to max 1, Sec. 5) on a power-law
+    graph, in the default and the two-solve mode."""
+    from paper_2101_08143_gb300 import fj
+    g = synth.chung_lu(12_000, 60_000, 2.2, seed=31, weighted=True)
+    gen = {"uniform": synth.opinions_uniform, "exponential": synth.opinions_exponential,
+           "power_law": synth.opinions_power_law}[dist]
+    s = gen(g.n, 2, 13)
+    zo, qo = _oracle(g, s)
+    o = fj.default_opts(tol=1e-10, flags=fj.FJ_TWO_SOLVES if two else 0)
+    with ctx.upload_edges(g) as dg:
+        z, q, _ = ctx.solve(dg, s, opts=o)
+    for j in range(2):
+        _check_quantities(q[j], qo[j], s[:, j], 1e-6)
+    np.testing.assert_allclose(z, zo, atol=1e-8)
+
+
 def test_two_solves_mode_rejected_where_unsupported(ctx):
     from paper_2101_08143_gb300 import fj
     g = synth.erdos_renyi(500, 2000, seed=4)
