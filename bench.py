@@ -202,6 +202,37 @@ def precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush, reps=
     return out
 
 
+def warm_start_run(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush, reps=5):
+    """Re-solve after 1% of the opinions change: cold (from 0) against warm
+    (fj_solve_warm from the previous z), both to the bench tolerance."""
+    rng = np.random.default_rng(23)
+    dev = src_d.device
+    s = torch.from_numpy(rng.random(g.n)).to(dev)
+    s2 = s.clone()
+    idx = torch.from_numpy(rng.choice(g.n, g.n // 100, replace=False)).to(dev)
+    s2[idx] = torch.from_numpy(rng.random(len(idx))).to(dev)
+    o = fj.default_opts(tol=TOL)
+    out = {}
+    with torch.cuda.stream(stream):
+        gr = ctx.upload(g.n, src_d, dst_d, w_d, merge_duplicates=MERGE)
+        z1, _, _ = ctx.solve(gr, s, opts=o)
+        for name, z0 in (("cold", None), ("warm", z1)):
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                _, _, info = ctx.solve(gr, s2, opts=o, want_z=False, z0=z0)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            out[name] = {"ms_per_call": float(np.median(ms)), "iterations": info["iterations"],
+                         "rel_residual": info["rel_residual"]}
+        gr.free()
+    out["change"] = "1% of the opinions redrawn"
+    return out
+
+
 def serving_run(ctx, fj, n_requests=240, seed=4, rate_frac=0.5):
     """A Poisson stream of requests that bring their own graph (Erdos-Renyi or
     Chung-Lu, n log-uniform in [10^3, 10^5], average degree U[4, 20],
@@ -445,6 +476,7 @@ def main():
     d2h = g.n * k * 8 + k * 5 * 8
 
     compare = precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush)
+    warm = warm_start_run(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush)
     serving = serving_run(ctx, fj) if not args.no_serving else None
 
     line = None
@@ -476,6 +508,7 @@ def main():
             "clocks": clk,
             "quantities": q[0],
             "precision_compare": compare,
+            "warm_start": warm,
             "serving": serving,
         }
     ctx.close()

@@ -194,6 +194,17 @@ fj_status fj_solve_ex(fj_ctx* ctx, const fj_graph* g, int32_t k,
                       const double* s, double* z, fj_quant* quant,
                       const fj_opts* opts, fj_info* info);
 
+/* fj_solve_ex started from an initial guess z0 instead of 0 (for example the
+ * z of an earlier solve, after s or a few weights changed).  The iteration
+ * starts at q = z0 - mu 1 with one float64 residual evaluation; the stopping
+ * rule, the results and their accuracy are those of fj_solve_ex, only the
+ * number of iterations depends on how close z0 is.
+ *   z0   float64[n*k], same layout and location as s (not modified)
+ * Errors: as fj_solve_ex; FJ_ERR_ARG for a NULL z0. */
+fj_status fj_solve_warm(fj_ctx* ctx, const fj_graph* g, int32_t k,
+                        const double* s, const double* z0, double* z,
+                        fj_quant* quant, const fj_opts* opts, fj_info* info);
+
 /* fj_solve_ex with quant = NULL: the equilibrium z = (I + L)^-1 s. */
 fj_status fj_solve(fj_ctx* ctx, const fj_graph* g, int32_t k, const double* s,
                    double* z, const fj_opts* opts, fj_info* info);

@@ -26,7 +26,7 @@ size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int n
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k,
                           const double* s, double* z, double* quant, double* resid, int* status,
                           char* ws, size_t ws_bytes, const fj_opts& o, int* launches_out,
-                          int max_blocks);
+                          int max_blocks, const double* z0);
 
 namespace fj {
 struct Server;
@@ -115,6 +115,8 @@ struct fj_ctx {
   size_t s_bytes = 0;
   double* z_dev = nullptr;
   size_t z_bytes = 0;
+  double* z0_dev = nullptr;  // staging of a host initial guess
+  size_t z0_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int max_blocks = 0;  // 0: all co-resident blocks
   std::mutex server_mu;
@@ -225,6 +227,7 @@ fj_status fj_destroy(fj_ctx* c) {
   if (c->small) cudaFree(c->small);
   if (c->s_dev) cudaFree(c->s_dev);
   if (c->z_dev) cudaFree(c->z_dev);
+  if (c->z0_dev) cudaFree(c->z0_dev);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own) cudaStreamDestroy(c->own);
@@ -326,8 +329,8 @@ fj_status fj_graph_stats(const fj_graph* g, int64_t* n, int64_t* nnz, int32_t* w
   return FJ_OK;
 }
 
-fj_status fj_solve_ex(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, double* z,
-                      fj_quant* quant, const fj_opts* opts, fj_info* info) {
+static fj_status solve_impl(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, const double* z0,
+                            double* z, fj_quant* quant, const fj_opts* opts, fj_info* info) {
   if (info) memset(info, 0, sizeof(*info));
   if (!c || !g || !s || k < 1) {
     set_error("fj_solve: ctx, graph and s must be non-NULL and k >= 1");
@@ -374,6 +377,12 @@ fj_status fj_solve_ex(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, 
     if (rc != FJ_OK) return rc;
     FJ_CUDA(cudaMemcpyAsync(c->s_dev, s, vec_bytes, cudaMemcpyHostToDevice, c->stream));
     sd = c->s_dev;
+    if (z0) {
+      rc = grow((void**)&c->z0_dev, &c->z0_bytes, vec_bytes);
+      if (rc != FJ_OK) return rc;
+      FJ_CUDA(cudaMemcpyAsync(c->z0_dev, z0, vec_bytes, cudaMemcpyHostToDevice, c->stream));
+      z0 = c->z0_dev;
+    }
     if (z) {
       rc = grow((void**)&c->z_dev, &c->z_bytes, vec_bytes);
       if (rc != FJ_OK) return rc;
@@ -384,7 +393,7 @@ fj_status fj_solve_ex(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, 
   FJ_CUDA(cudaEventRecord(c->ev0, c->stream));
   int done_launches = 0;
   rc = fj_solve_device(g, c->stream, c->num_sms, k, sd, zd, dq, dres, dstat, c->ws, c->ws_bytes, o,
-                       &done_launches, c->max_blocks);
+                       &done_launches, c->max_blocks, z0);
   if (rc != FJ_OK) return rc;
   FJ_CUDA(cudaEventRecord(c->ev1, c->stream));
   std::vector<double> hq((size_t)cols * 5), hres(cols);
@@ -428,6 +437,21 @@ fj_status fj_solve_ex(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, 
     info->columns = k;
   }
   return rc;
+}
+
+fj_status fj_solve_ex(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, double* z,
+                      fj_quant* quant, const fj_opts* opts, fj_info* info) {
+  return solve_impl(c, g, k, s, nullptr, z, quant, opts, info);
+}
+
+fj_status fj_solve_warm(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, const double* z0,
+                        double* z, fj_quant* quant, const fj_opts* opts, fj_info* info) {
+  if (!z0) {
+    if (info) memset(info, 0, sizeof(*info));
+    set_error("fj_solve_warm: z0 must be non-NULL");
+    return FJ_ERR_ARG;
+  }
+  return solve_impl(c, g, k, s, z0, z, quant, opts, info);
 }
 
 fj_status fj_solve(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, double* z,

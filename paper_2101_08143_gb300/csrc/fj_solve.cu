@@ -90,6 +90,8 @@ struct SolveParams {
   // (2j: s_j solved as is, 2j+1: s_j centred), source column = c >> col_shift
   int paper;
   int col_shift;
+  // warm start: initial guess z0 (same layout as s) or null
+  const double* z0;
 };
 
 // Grid-wide barrier with a bounded wait.  The counter only grows: barrier
@@ -297,6 +299,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
     __syncthreads();
   }
 
+  // float64 residual walk: t64 = L q (off-diagonal part of (I + L) q) and
+  // this block's part of sum w (q_i - q_j)^2, then the barrier
+  auto residual_walk = [&]() -> bool {
+    double quad;
+    if constexpr (kWide) {
+      wide_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, P.unit_counter, unit_base, P.quad_u, my_sxr64);
+      unit_base += unit_step;
+      if (!grid_sync(P.bar, status, epoch)) return false;
+      quad = unit_sum<K>(P.quad_u, u0, u1);
+    } else {
+      df64 qd[K];
+#pragma unroll
+      for (int cc = 0; cc < K; ++cc) qd[cc] = df_from_float(0.0f);
+      sell_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, u0, u1, qd);
+      quad = lane_share<df64, K>(qd);
+    }
+    const double v[1] = {quad};
+    const int sl[1] = {S_D};
+    block_store<K, 1>(v, sl, P.part, red);
+    return grid_sync(P.bar, status, epoch);
+  };
+
+  // warm start: q = z0 - mu 1, and its residual walk
+  const bool warm = P.z0 != nullptr;
+  if (warm) {
+    for (int64_t idx = gtid; idx < NK; idx += gstride)
+      P.q[idx] = df_from_double(P.z0[(int64_t)(c >> P.col_shift) * P.ld + P.perm[idx / K]] - mu[c]);
+    if (!grid_sync(P.bar, status, epoch)) return;
+    if (!residual_walk()) return;
+  }
+
   int iters = 0, refines = 0;
   bool init = true;
   while (true) {
@@ -318,10 +351,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
           const double sbd = P.s[(int64_t)(c >> P.col_shift) * P.ld + P.perm[i]] - m;
           sb = df_from_double(sbd);
           P.sbar[idx] = sb;
-          P.q[idx] = z0;
-          qv = z0;
-          lq = z0;
           a_bb += sbd * sbd;
+          if (warm) {
+            qv = P.q[idx];
+            lq = row_t<df64, K>(P.sg, P.t64, P.hub_part64, i, idx, c);
+          } else {
+            P.q[idx] = z0;
+            qv = z0;
+            lq = z0;
+          }
         } else {
           sb = P.sbar[idx];
           qv = P.q[idx];
@@ -362,7 +400,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       if (init) {
         const int sb[1] = {S_BB};
         grid_reduce<K, 1>(sb, P.part, res);
-      } else {
+      }
+      if (!init || warm) {
         const int sd[1] = {S_D};
         grid_reduce<K, 1>(sd, P.part, res);
       }
@@ -377,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       if (!finite(rr64)) atomicOr(status, kErrNumeric);
       // quantities of the current iterate (final after the last pass)
       if (blockIdx.x == 0) {
-        const double D = init ? 0.0 : 0.5 * res[S_D * K + cc];
+        const double D = (init && !warm) ? 0.0 : 0.5 * res[S_D * K + cc];
         const double C = res[S_C * K + cc];
         P.quant[cc * 5 + 0] = res[S_CI * K + cc];
         P.quant[cc * 5 + 1] = D;
@@ -577,28 +616,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         P.q[idx] = df_add(P.q[idx], df_from_double((double)P.x[idx]));
     }
     if (!grid_sync(P.bar, status, epoch)) return;
-    {
-      double quad;
-      if constexpr (kSell) {
-        if constexpr (kWide) {
-          wide_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, P.unit_counter, unit_base, P.quad_u,
-                             my_sxr64);
-          unit_base += unit_step;
-          if (!grid_sync(P.bar, status, epoch)) return;
-          quad = unit_sum<K>(P.quad_u, u0, u1);
-        } else {
-          df64 qd[K];
-#pragma unroll
-          for (int cc = 0; cc < K; ++cc) qd[cc] = df_from_float(0.0f);
-          sell_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, u0, u1, qd);
-          quad = lane_share<df64, K>(qd);
-        }
-      }
-      const double v[1] = {quad};
-      const int sl[1] = {S_D};
-      block_store<K, 1>(v, sl, P.part, red);
-    }
-    if (!grid_sync(P.bar, status, epoch)) return;
+    if (!residual_walk()) return;
   }
 
   // ---------------------------------------------------------------- output
@@ -621,7 +639,7 @@ template <typename VI, int K>
 static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, const double* s,
                             int64_t ld, double* z, double* quant, double* resid, int* status,
                             char* ws, size_t ws_bytes, const fj_opts& o, int mode, int max_blocks,
-                            bool paper) {
+                            bool paper, const double* z0) {
   auto kern = k_solve<VI, K>;
   const size_t red_bytes = (size_t)7 * kWarps * K * sizeof(double);
   const size_t stage = (K <= 4) ? 0 : (size_t)kWarps * kWideStageBytes;
@@ -689,6 +707,7 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.max_refine = o.max_refine;
   P.mode = mode;
   P.paper = paper ? 1 : 0;
+  P.z0 = z0;
   P.col_shift = paper ? 1 : 0;
   FJ_CUDA(cudaMemsetAsync(P.bar, 0, 64, st));
   void* args[] = {&P};
@@ -725,7 +744,7 @@ size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int n
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k,
                           const double* s, double* z, double* quant, double* resid, int* status,
                           char* ws, size_t ws_bytes, const fj_opts& o, int* launches_out,
-                          int max_blocks) {
+                          int max_blocks, const double* z0) {
   int mode = o.precision == FJ_PREC_FP64 ? kModeFP64 : (o.precision == FJ_PREC_FP32 ? kModeFP32 : kModeMixed);
   // two-solve mode: 2k launch columns (s_j as is, s_j centred), quant and
   // resid per launch column; every launch starts at an even column
@@ -739,6 +758,7 @@ fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32
     const int64_t src_col = paper ? col / 2 : col;
     const double* sc = s + src_col * g->n;
     double* zc = z ? z + src_col * g->n : nullptr;
+    const double* z0c = z0 ? z0 + src_col * g->n : nullptr;
     double* qc = quant + (int64_t)col * 5;
     double* rc = resid + col;
     int* stc = status + 3 * li;
@@ -746,10 +766,10 @@ fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32
 #define FJ_LAUNCH(KK)                                                                                  \
   if (mode == kModeFP64)                                                                               \
     rcode = launch_one<double, KK>(g, st, num_sms, sc, g->n, zc, qc, rc, stc, ws, ws_bytes, o, mode,   \
-                                   max_blocks, paper);                                                 \
+                                   max_blocks, paper, z0c);                                            \
   else                                                                                                 \
     rcode = launch_one<float, KK>(g, st, num_sms, sc, g->n, zc, qc, rc, stc, ws, ws_bytes, o, mode,    \
-                                  max_blocks, paper);
+                                  max_blocks, paper, z0c);
     switch (K) {
       case 32: FJ_LAUNCH(32) break;
       case 16: FJ_LAUNCH(16) break;
@@ -857,7 +877,7 @@ extern "C" fj_status fj_solve_fixed(const fj_graph* g, void* stream, int32_t k, 
   od.flags = FJ_DEVICE_PTRS;
   int done = 0;
   rc = fj_solve_device(g, st, num_sms, k, s, z, dq, dres, dstat, base + head, FJ_FIXED_SCRATCH_BYTES - head, od,
-                       &done, 0);
+                       &done, 0, nullptr);
   if (rc != FJ_OK) return rc;
   double hq[32 * 5], hres[32];
   int hstat[3 * 6];

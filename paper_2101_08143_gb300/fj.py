@@ -81,6 +81,8 @@ _SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int32)]),
     "fj_solve_ex": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P,
                                      ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
+    "fj_solve_warm": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, _P,
+                                       ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
     "fj_solve": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P,
                                   ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
     "fj_quantities": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P,
@@ -223,13 +225,14 @@ class Context:
 
     # -------------------------------------------------------------- solve
     def solve(self, graph: Graph, s, want_z=True, want_quant=True, opts: Opts | None = None,
-              z_out=None, raise_on_error=True):
+              z_out=None, raise_on_error=True, z0=None):
         """Solve (I + L) z = s for the columns of s.
 
         s: numpy float64 (n,) or (n, k) [host], or a torch float64 CUDA tensor
         of shape (k, n) / (n,) whose rows are the columns (column-major n x k
         memory) [device].  Returns (z, quantities, info); z is a numpy (n, k)
         array for host input, or the z_out / new torch tensor for device input.
+        z0: optional initial guess in the same form as s (fj_solve_warm).
         """
         lib = load()
         o = Opts() if opts is None else opts
@@ -248,6 +251,10 @@ class Context:
             if want_z:
                 z = z_out if z_out is not None else torch.empty_like(s)
             sp, zp = s.data_ptr(), (z.data_ptr() if z is not None else None)
+            if z0 is not None and (not z0.is_contiguous() or z0.dtype != torch.float64
+                                   or z0.numel() != n * k):
+                raise ValueError("device z0 must be contiguous float64 shaped like s")
+            z0p = z0.data_ptr() if z0 is not None else None
             o.flags = (o.flags & ~FJ_DEVICE_PTRS) | FJ_DEVICE_PTRS
             keep = None
         else:
@@ -267,15 +274,22 @@ class Context:
             sp = sf.ctypes.data
             zp = z.ctypes.data if z is not None else None
             o.flags = (o.flags & ~FJ_DEVICE_PTRS) | FJ_HOST_PTRS
-            keep = sf
+            z0f = None if z0 is None else np.asfortranarray(
+                np.asarray(z0, dtype=np.float64).reshape(n, k))
+            z0p = z0f.ctypes.data if z0f is not None else None
+            keep = (sf, z0f)
         quant = (Quant * k)() if want_quant else None
         info = Info()
-        rc = lib.fj_solve_ex(self.handle, graph.handle, k, _P(sp), _P(zp),
-                             ctypes.cast(quant, _P) if quant is not None else None,
-                             ctypes.byref(o), ctypes.byref(info))
+        qp = ctypes.cast(quant, _P) if quant is not None else None
+        if z0 is None:
+            rc = lib.fj_solve_ex(self.handle, graph.handle, k, _P(sp), _P(zp), qp,
+                                 ctypes.byref(o), ctypes.byref(info))
+        else:
+            rc = lib.fj_solve_warm(self.handle, graph.handle, k, _P(sp), _P(z0p), _P(zp), qp,
+                                   ctypes.byref(o), ctypes.byref(info))
         del keep
         if raise_on_error:
-            _check(rc, "fj_solve_ex")
+            _check(rc, "fj_solve_ex" if z0 is None else "fj_solve_warm")
         qs = None
         if quant is not None:
             qs = [{name: getattr(quant[j], name) for name in QUANTITY_NAMES} for j in range(k)]

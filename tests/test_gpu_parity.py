@@ -200,6 +200,35 @@ def test_paper_opinion_distributions(ctx, dist, two):
     np.testing.assert_allclose(z, zo, atol=1e-8)
 
 
+@pytest.mark.parametrize("k,two", [(1, False), (5, False), (2, True)])
+def test_warm_start(ctx, k, two):
+    """fj_solve_warm: from the exact answer it stops at once; from the answer
+    for a slightly changed s it needs fewer iterations than a cold solve and
+    matches the oracle; from a poor guess it still converges."""
+    from paper_2101_08143_gb300 import fj
+    g = synth.chung_lu(20_000, 100_000, 2.2, seed=41, weighted=True)
+    s = synth.opinions_uniform(g.n, k, 8)
+    o = fj.default_opts(tol=1e-10, flags=fj.FJ_TWO_SOLVES if two else 0)
+    s2 = s.copy()
+    rng = np.random.default_rng(2)
+    idx = rng.choice(g.n, g.n // 100, replace=False)
+    s2[idx] = rng.random((len(idx), k))  # 1% of the opinions change
+    zo, qo = _oracle(g, s2)
+    with ctx.upload_edges(g) as dg:
+        z1, _, info1 = ctx.solve(dg, s, opts=o)
+        _, _, again = ctx.solve(dg, s, opts=o, z0=z1)
+        assert again["iterations"] == 0 and again["rel_residual"] <= 1e-10
+        zc, qc, cold = ctx.solve(dg, s2, opts=o)
+        zw, qw, warm = ctx.solve(dg, s2, opts=o, z0=z1)
+        _, qp, poor = ctx.solve(dg, s2, opts=o, z0=-5.0 * np.ones_like(s2))
+    assert warm["rel_residual"] <= 1e-10 and poor["rel_residual"] <= 1e-10
+    assert warm["iterations"] < cold["iterations"]
+    for j in range(k):
+        for qq in (qw, qp, qc):
+            _check_quantities(qq[j], qo[j], s2[:, j], 1e-6)
+    np.testing.assert_allclose(zw, zo, atol=1e-8)
+
+
 def test_two_solves_mode_rejected_where_unsupported(ctx):
     from paper_2101_08143_gb300 import fj
     g = synth.erdos_renyi(500, 2000, seed=4)
