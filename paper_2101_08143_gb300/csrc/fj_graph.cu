@@ -33,6 +33,7 @@ constexpr int kSortChunk = kSortThreads * kSortItems;
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanThreads * kScanItems;
+constexpr int64_t kScanDirectTiles = 1024;
 
 // ------------------------------------------------------------ validation
 
@@ -292,10 +293,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* __restric
   if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
+// offs: the tiles' scanned offsets, or (sums_in) their unscanned sums, which
+// warp 0 adds up for the tiles before this one (few tiles only).
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(T* __restrict__ data, int64_t cnt,
-                                                             const T* __restrict__ offs) {
+                                                             const T* __restrict__ offs, bool sums_in) {
   __shared__ T sh[kScanThreads / 32];
+  __shared__ T tile_off;
   const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
   T vals[kScanItems];
   T v = 0;
@@ -303,8 +307,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(T* __restrict__ dat
     vals[i] = (base + i < cnt) ? data[base + i] : T(0);
     v += vals[i];
   }
+  if (threadIdx.x < 32) {
+    T o = 0;
+    if (offs && sums_in) {
+      for (int64_t b = threadIdx.x; b < (int64_t)blockIdx.x; b += 32) o += offs[b];
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) o += __shfl_xor_sync(kFull, o, d);
+    } else if (offs) {
+      o = offs[blockIdx.x];
+    }
+    if (threadIdx.x == 0) tile_off = o;
+  }
   T total;
-  T run = block_exclusive_scan<T>(v, sh, total) + (offs ? offs[blockIdx.x] : T(0));
+  T run = block_exclusive_scan<T>(v, sh, total) + tile_off;
   for (int i = 0; i < kScanItems; ++i) {
     if (base + i < cnt) data[base + i] = run;
     run += vals[i];
@@ -318,7 +333,7 @@ static fj_status exclusive_scan(T* data, int64_t cnt, cudaStream_t st) {
   const int64_t blocks = (cnt + kScanChunk - 1) / kScanChunk;
   if (blocks == 1) {
     count_launches(1);
-    k_scan_apply<T><<<1, kScanThreads, 0, st>>>(data, cnt, nullptr);
+    k_scan_apply<T><<<1, kScanThreads, 0, st>>>(data, cnt, nullptr, false);
     FJ_CUDA(cudaGetLastError());
     return FJ_OK;
   }
@@ -326,10 +341,13 @@ static fj_status exclusive_scan(T* data, int64_t cnt, cudaStream_t st) {
   FJ_CUDA(malloc_async(&sums, blocks * sizeof(T), st));
   count_launches(1);
   k_scan_reduce<T><<<(unsigned)blocks, kScanThreads, 0, st>>>(data, cnt, sums);
-  fj_status rc = exclusive_scan<T>(sums, blocks, st);
+  // up to kScanDirectTiles tiles, each block adds its predecessors' sums
+  // itself; beyond that the tile sums are scanned first
+  const bool direct = blocks <= kScanDirectTiles;
+  fj_status rc = direct ? FJ_OK : exclusive_scan<T>(sums, blocks, st);
   if (rc == FJ_OK) {
     count_launches(1);
-    k_scan_apply<T><<<(unsigned)blocks, kScanThreads, 0, st>>>(data, cnt, sums);
+    k_scan_apply<T><<<(unsigned)blocks, kScanThreads, 0, st>>>(data, cnt, sums, direct);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "k_scan_apply");
   }
