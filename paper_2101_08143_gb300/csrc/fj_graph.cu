@@ -10,9 +10,10 @@
 //      saturated degree keys), which fixes the solver-order row pointers and
 //      the SpMV layouts: chunks of the long rows, sliced ELL for the rest,
 //      and the work units;
-//   3. a stable LSD radix sort of the 2m entries by solver-order row puts
-//      every entry at its CSR position, rows keeping the input order of their
-//      entries, and its last pass also writes the sliced-ELL copy;
+//   3. one streaming pass writes the 2m directed entries in solver
+//      numbering; a stable LSD radix sort of them by row puts every entry at
+//      its CSR position, rows keeping the input order of their entries, and
+//      its last pass also writes the sliced-ELL copy;
 //   4. the Jacobi preconditioner 1 / (1 + d_i).
 // The graph, and every sum over it, is therefore the same bits on every
 // upload.  The host waits once, at the end, for the sizes and the
@@ -61,34 +62,40 @@ __global__ void k_validate_degree(int64_t m, int64_t n, const int32_t* __restric
 
 // ------------------------------------------------------------- radix sort
 
-// One directed entry: key = solver-order row id (n for a self-loop or an
-// invalid edge), col = solver-order column, weight.
+// Sort input: key = solver-order row id (n for a self-loop or an invalid
+// edge), col = solver-order column, weight (null: unit weights).
 struct EntrySrc {
-  const int32_t* src;      // edge list (first pass) ...
-  const int32_t* dst;
-  const float* w;
-  const int32_t* old2new;  // input id -> solver id
-  const int32_t* key;      // ... or sorted arrays (later passes)
+  const int32_t* key;
   const int32_t* col;
   const float* val;
   int32_t n;
 };
 
-template <bool FROM_EDGES>
-__device__ __forceinline__ void load_entry(const EntrySrc& s, int64_t p, int32_t& key,
-                                           int32_t& col, float& val) {
-  if (FROM_EDGES) {
-    const int64_t e = p >> 1;
-    const int32_t u = s.src[e], v = s.dst[e];
-    const bool side = p & 1;
-    const bool ok = u != v && u >= 0 && u < s.n && v >= 0 && v < s.n;
-    key = ok ? s.old2new[side ? v : u] : s.n;
-    col = ok ? s.old2new[side ? u : v] : 0;
-    val = s.w ? s.w[e] : 1.0f;
-  } else {
-    key = s.key[p];
-    col = s.col[p];
-    val = s.val ? s.val[p] : 1.0f;
+__device__ __forceinline__ void load_entry(const EntrySrc& s, int64_t p, int32_t& key, int32_t& col,
+                                           float& val) {
+  key = s.key[p];
+  col = s.col[p];
+  val = s.val ? s.val[p] : 1.0f;
+}
+
+// The directed entries of the edge list in solver numbering: entry 2e is
+// (new(u), new(v)), entry 2e+1 is (new(v), new(u)), both of weight w_e; a
+// self-loop or an invalid edge gets the key n (sorted past the last row).
+__global__ void k_make_entries(int64_t m, int32_t n, const int32_t* __restrict__ src,
+                               const int32_t* __restrict__ dst, const float* __restrict__ w,
+                               const int32_t* __restrict__ old2new, int2* __restrict__ key2,
+                               int2* __restrict__ col2, float2* __restrict__ val2) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = src[e], v = dst[e];
+    const bool ok = u != v && u >= 0 && u < n && v >= 0 && v < n;
+    const int32_t nu = ok ? old2new[u] : n, nv = ok ? old2new[v] : n;
+    key2[e] = make_int2(nu, nv);
+    col2[e] = ok ? make_int2(nv, nu) : make_int2(0, 0);
+    if (val2) {
+      const float x = w[e];
+      val2[e] = make_float2(x, x);
+    }
   }
 }
 
@@ -104,7 +111,6 @@ struct EntryDst {
   float* sell_val;
 };
 
-template <bool FROM_EDGES>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t N, int shift,
                                                              int32_t* __restrict__ hist) {
   __shared__ int h[256];
@@ -116,7 +122,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t
     if (p < N) {
       int32_t key, col;
       float val;
-      load_entry<FROM_EDGES>(s, p, key, col, val);
+      load_entry(s, p, key, col, val);
       atomicAdd(&h[(key >> shift) & 255], 1);
     }
   }
@@ -139,7 +145,7 @@ struct ScatterSmem {
   int start[256];
 };
 
-template <bool FROM_EDGES, bool LAST>
+template <bool LAST>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int64_t N, int shift,
                                                                 const int32_t* __restrict__ offs,
                                                                 int32_t* __restrict__ okey,
@@ -163,7 +169,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
     key[r] = 0;
     col[r] = 0;
     val[r] = 0.f;
-    if (valid) load_entry<FROM_EDGES>(s, cbase + li, key[r], col[r], val[r]);
+    if (valid) load_entry(s, cbase + li, key[r], col[r], val[r]);
   }
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
@@ -684,14 +690,13 @@ static unsigned grid_for(int64_t work, int threads) {
   return (unsigned)b;
 }
 
-// Stable LSD radix sort (8-bit digits) of N entries by key in [0, key_max].
-// FROM_EDGES: entries are generated from the edge list (first pass only).
-// Buffers kb/cb/vb[2] must hold N + kPad elements (vb may be null: no val);
-// returns the index (0/1) of the buffer set holding the result.  With
-// `last`, the last pass writes the CSR and sliced ELL instead.
-static fj_status radix_sort(EntrySrc src, bool from_edges, int64_t N, int64_t key_max, int32_t* kb[2],
-                            int32_t* cb[2], float* vb[2], const EntryDst* last, cudaStream_t st,
-                            int* result) {
+// Stable LSD radix sort (8-bit digits) of N entries by key in [0, key_max],
+// from buffer set 0.  Buffers kb/cb/vb[2] must hold N + kPad elements (vb
+// may be null: no val); returns the index (0/1) of the buffer set holding
+// the result.  With `last`, the last pass writes the CSR and sliced ELL
+// instead.
+static fj_status radix_sort(int32_t n, int64_t N, int64_t key_max, int32_t* kb[2], int32_t* cb[2], float* vb[2],
+                            const EntryDst* last, cudaStream_t st, int* result) {
   int bits = 1;
   while ((int64_t(1) << bits) <= key_max) ++bits;
   const int passes = (bits + 7) / 8;
@@ -705,21 +710,12 @@ static fj_status radix_sort(EntrySrc src, bool from_edges, int64_t N, int64_t ke
   const size_t ssm = sizeof(ScatterSmem);
   const EntryDst none{};
   for (int pass = 0; pass < passes && rc == FJ_OK; ++pass) {
-    const bool edges = from_edges && pass == 0;
     const bool fin = last && pass == passes - 1;
-    EntrySrc s = src;
-    if (!edges) {
-      s.key = kb[cur];
-      s.col = cb[cur];
-      s.val = vb[cur];
-    }
-    const int dstb = edges ? 0 : 1 - cur;
+    const EntrySrc s{kb[cur], cb[cur], vb[cur], n};
+    const int dstb = 1 - cur;
     const int shift = pass * 8;
     count_launches(2);
-    if (edges)
-      k_radix_hist<true><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, shift, h);
-    else
-      k_radix_hist<false><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, shift, h);
+    k_radix_hist<<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, shift, h);
     rc = exclusive_scan<int32_t>(h, 256 * nblocks, st);
     if (rc != FJ_OK) break;
     const EntryDst& d = fin ? *last : none;
@@ -727,14 +723,10 @@ static fj_status radix_sort(EntrySrc src, bool from_edges, int64_t N, int64_t ke
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
       kern<<<(unsigned)nblocks, kSortThreads, ssm, st>>>(s, N, shift, h, kb[dstb], cb[dstb], vb[dstb], d);
     };
-    if (edges && fin)
-      launch(k_radix_scatter<true, true>);
-    else if (edges)
-      launch(k_radix_scatter<true, false>);
-    else if (fin)
-      launch(k_radix_scatter<false, true>);
+    if (fin)
+      launch(k_radix_scatter<true>);
     else
-      launch(k_radix_scatter<false, false>);
+      launch(k_radix_scatter<false>);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "radix sort");
     cur = dstb;
@@ -822,9 +814,8 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   count_launches(1);
   k_degree_keys<<<grid_for(n, 256), 256, 0, st>>>(deg, n, kb2[0], cb2[0]);
   FJ_CUDA(cudaGetLastError());
-  EntrySrc ns{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, (int32_t)n};
   int cur2 = 0;
-  fj_status rc = radix_sort(ns, false, n, kDegKeyMax, kb2, cb2, vb2, nullptr, st, &cur2);
+  fj_status rc = radix_sort((int32_t)n, n, kDegKeyMax, kb2, cb2, vb2, nullptr, st, &cur2);
   if (rc != FJ_OK) return rc;
   int32_t* perm = cb2[cur2];
 
@@ -909,10 +900,17 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
       if (weighted) vb[i] = sort_pool.get<float>(cap);
     }
     if (sort_pool.failed) return fail(oom());
-    EntrySrc es{src, dst, w, old2new, nullptr, nullptr, nullptr, (int32_t)n};
+    if (m > 0) {
+      count_launches(1);
+      k_make_entries<<<grid_for(m, 256), 256, 0, st>>>(m, (int32_t)n, src, dst, w, old2new,
+                                                        reinterpret_cast<int2*>(kb[0]),
+                                                        reinterpret_cast<int2*>(cb[0]),
+                                                        reinterpret_cast<float2*>(vb[0]));
+      if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
+    }
     EntryDst ed{g->col, g->val, g->row_ptr, dcnt, g->slice_off, g->sell_col, g->sell_val};
     int cur = 0;
-    rc = radix_sort(es, true, N, n, kb, cb, vb, &ed, st, &cur);
+    rc = radix_sort((int32_t)n, N, n, kb, cb, vb, &ed, st, &cur);
     if (rc != FJ_OK) return fail(rc);
   }
 
