@@ -131,9 +131,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t
 }
 
 // Stable scatter of one chunk of kSortChunk items.  Items are ranked in
-// input order (rounds of kSortThreads items: by warp, then by lane), placed
-// in shared memory in digit order, and written out as one contiguous run per
-// digit, so that global stores are coalesced.  LAST: the sorted position is
+// input order (by warp, then round, then lane), placed in shared memory in
+// digit order, and written out as one contiguous run per digit, so that
+// global stores are coalesced.  LAST: the sorted position is
 // the entry's CSR position; write the CSR and sliced-ELL copies instead of
 // the sort buffers (entries keyed n are dropped).
 struct ScatterSmem {
@@ -158,43 +158,48 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
   const unsigned lt_mask = (1u << lane) - 1u;
   const int64_t cbase = (int64_t)blockIdx.x * kSortChunk;
   const int cnt = (int)((N - cbase) < kSortChunk ? (N - cbase) : kSortChunk);
-  for (int i = tid; i < 256; i += kSortThreads) sm.run[i] = 0;
+  // warp w holds chunk items w*256 + r*32 + lane (r < kSortItems), so the
+  // input order is (warp, round, lane): each warp ranks its own items
+  // against warp-private digit counters, and one block-wide pass turns the
+  // counters into per-warp offsets
+  for (int j = lane; j < 256; j += 32) sm.wcnt[warp][j] = 0;
   int32_t key[kSortItems], col[kSortItems];
   float val[kSortItems];
   int rank[kSortItems];
+  const int wbase = warp * 32 * kSortItems;
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    const int li = r * kSortThreads + tid;
-    const bool valid = li < cnt;
+    const int li = wbase + r * 32 + lane;
     key[r] = 0;
     col[r] = 0;
     val[r] = 0.f;
-    if (valid) load_entry(s, cbase + li, key[r], col[r], val[r]);
+    if (li < cnt) load_entry(s, cbase + li, key[r], col[r], val[r]);
   }
+  __syncwarp();
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    const bool valid = r * kSortThreads + tid < cnt;
+    const bool valid = wbase + r * 32 + lane < cnt;
     const int digit = valid ? ((key[r] >> shift) & 255) : 256;
-    for (int j = lane; j < 256; j += 32) sm.wcnt[warp][j] = 0;
-    __syncwarp();
     const unsigned peers = __match_any_sync(kFull, digit);
     const int rk = __popc(peers & lt_mask);
-    if (valid && rk == 0) sm.wcnt[warp][digit] = __popc(peers);
-    __syncthreads();
-    if (tid < 256) {
-      int acc = sm.run[tid];
-#pragma unroll
-      for (int w = 0; w < kW; ++w) {
-        const int c = sm.wcnt[w][tid];
-        sm.wcnt[w][tid] = acc;
-        acc += c;
-      }
-      sm.run[tid] = acc;
-    }
-    __syncthreads();
-    rank[r] = valid ? sm.wcnt[warp][digit] + rk : 0;
-    __syncthreads();
+    const int before = valid ? sm.wcnt[warp][digit] : 0;
+    __syncwarp();
+    if (valid && rk == 0) sm.wcnt[warp][digit] = before + __popc(peers);
+    __syncwarp();
+    rank[r] = before + rk;
   }
+  __syncthreads();
+  if (tid < 256) {  // per digit: offsets of the warps' runs, and the total
+    int acc = 0;
+#pragma unroll
+    for (int w = 0; w < kW; ++w) {
+      const int c = sm.wcnt[w][tid];
+      sm.wcnt[w][tid] = acc;
+      acc += c;
+    }
+    sm.run[tid] = acc;
+  }
+  __syncthreads();
   // chunk-local start of every digit: exclusive scan of the 256 counts
   if (warp == 0) {
     int v[8], sum = 0;
@@ -219,9 +224,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    if (r * kSortThreads + tid < cnt) {
+    if (wbase + r * 32 + lane < cnt) {
       const int digit = (key[r] >> shift) & 255;
-      const int pos = sm.start[digit] + rank[r];
+      const int pos = sm.start[digit] + sm.wcnt[warp][digit] + rank[r];
       sm.key[pos] = key[r];
       sm.col[pos] = col[r];
       sm.val[pos] = val[r];
