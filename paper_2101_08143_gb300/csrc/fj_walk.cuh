@@ -112,10 +112,31 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
   const int lane = threadIdx.x & 31;
   // entries in flight per lane between two dependent round trips
   constexpr int kB = (K * sizeof(T) <= 4) ? 8 : 4;
-  for (int64_t u = u0; u < u1; ++u) {
+  // bounds of unit u: a chunk's row and entry range, or a slice's offsets;
+  // those of the next unit are loaded while the current one runs
+  auto bounds = [&](int64_t u, int32_t& r, int64_t& lo, int64_t& hi) {
     if (u < g.n_chunks) {
-      const int32_t r = g.chunk_row[u];
-      const int32_t b = g.chunk_begin[u], e = g.chunk_end[u];
+      r = g.chunk_row[u];
+      lo = g.chunk_begin[u];
+      hi = g.chunk_end[u];
+    } else {
+      const int64_t s = u - g.n_chunks;
+      r = 0;
+      lo = g.slice_off[s];
+      hi = g.slice_off[s + 1];
+    }
+  };
+  int32_t r_next = 0;
+  int64_t lo_next = 0, hi_next = 0;
+  if (u0 < u1) bounds(u0, r_next, lo_next, hi_next);
+  for (int64_t u = u0; u < u1; ++u) {
+    const int32_t r_cur = r_next;
+    const int64_t lo_cur = lo_next, hi_cur = hi_next;
+    if (u + 1 < u1) bounds(u + 1, r_next, lo_next, hi_next);
+    if (u < g.n_chunks) {
+      const int32_t r = r_cur;
+      const int32_t b = (int32_t)lo_cur, e = (int32_t)hi_cur;
+      const int32_t nch = g.long_first[r + 1] - g.long_first[r];
       T xr[K], acc[K];
       load_k<T, K>(x + (int64_t)r * K, xr);
 #pragma unroll
@@ -155,12 +176,11 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
         if (lane == cc) mine = acc[cc];
       // a row of one chunk is final; chunks of longer rows leave partial
       // sums, which the next phase adds up in chunk order (row_t)
-      const int32_t nch = g.long_first[r + 1] - g.long_first[r];
       if (lane < K) (nch == 1 ? out[(int64_t)r * K + lane] : part[u * K + lane]) = mine;
     } else {
       const int64_t s = u - g.n_chunks;
-      const int64_t off = g.slice_off[s];
-      const int32_t len = (int32_t)((g.slice_off[s + 1] - off) >> 5);
+      const int64_t off = lo_cur;
+      const int32_t len = (int32_t)((hi_cur - off) >> 5);
       const int64_t row = g.n_long + 32 * s + lane;
       if (row < g.n) {
         T xr[K], acc[K];
