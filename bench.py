@@ -239,7 +239,8 @@ def serving_run(ctx, fj, n_requests=240, seed=4, rate_frac=0.5):
     Chung-Lu, n log-uniform in [10^3, 10^5], average degree U[4, 20],
     weights U(0,1], 1-16 opinion vectors) through fj_submit_edges / fj_poll.
     First the saturation throughput (all requests at once), then an open
-    loop at rate_frac of it; latency = submit to completion."""
+    loop at rate_frac of it; latency = submit to completion.  The generated
+    graphs are simple, so requests pass FJ_MERGE_DUPLICATES."""
     import threading
     rng = np.random.default_rng(seed)
     pool = []
@@ -278,7 +279,7 @@ def serving_run(ctx, fj, n_requests=240, seed=4, rate_frac=0.5):
                 while time.perf_counter() < target:
                     time.sleep(max(0.0, min(0.001, target - time.perf_counter())))
             t_sub[i] = time.perf_counter()
-            tickets[i] = fj.submit_edges(ctx, gg.n, gg.src, gg.dst, gg.w, sv)
+            tickets[i] = fj.submit_edges(ctx, gg.n, gg.src, gg.dst, gg.w, sv, merge_duplicates=MERGE)
             ready.release()
         th.join()
         lat = 1000.0 * (np.array(t_done) - np.array(t_sub))
