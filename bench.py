@@ -234,6 +234,25 @@ def warm_start_run(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush, reps=5):
     return out
 
 
+def lcc_run(ctx, torch, g, src_d, dst_d, w_d, stream, reps=3):
+    """fj_graph_lcc on the bench graph: extraction time and the component's
+    size (the paper's experiments run on largest connected components)."""
+    out = {}
+    with torch.cuda.stream(stream):
+        gr = ctx.upload(g.n, src_d, dst_d, w_d, merge_duplicates=MERGE)
+        ms = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lg = gr.lcc()
+            ms.append(1000 * (time.perf_counter() - t0))
+            st = lg.stats()
+            lg.free()
+        gr.free()
+    out = {"ms": float(np.median(ms)), "n": st["n"], "nnz": st["nnz"], "of_n": g.n}
+    return out
+
+
 def serving_run(ctx, fj, n_requests=240, seed=4, rate_frac=0.5):
     """A Poisson stream of requests that bring their own graph (Erdos-Renyi or
     Chung-Lu, n log-uniform in [10^3, 10^5], average degree U[4, 20],
@@ -479,6 +498,7 @@ def main():
 
     compare = precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush)
     warm = warm_start_run(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush)
+    lcc = lcc_run(ctx, torch, g, src_d, dst_d, w_d, stream)
     serving = serving_run(ctx, fj) if not args.no_serving else None
 
     line = None
@@ -511,6 +531,7 @@ def main():
             "quantities": q[0],
             "precision_compare": compare,
             "warm_start": warm,
+            "lcc": lcc,
             "serving": serving,
         }
     ctx.close()

@@ -174,6 +174,21 @@ fj_status fj_graph_upload(fj_ctx* ctx, int64_t n, int64_t m,
 /* Frees a graph made by fj_graph_upload on this context. */
 fj_status fj_graph_free(fj_ctx* ctx, fj_graph* g);
 
+/* The subgraph induced on the largest connected component of g (the
+ * paper's experiments run on each network's largest connected component,
+ * Sec. 5).  Its nodes are those of the component in increasing order of
+ * their id in g; fj_graph_node_ids gives that map.  Of components of equal
+ * size, the one holding the smallest id wins.  Weights carry over.  *out
+ * lives until fj_graph_free.
+ * Errors: FJ_ERR_ARG, FJ_ERR_OOM, FJ_ERR_NOT_CONVERGED (the components did not
+ * settle within the round cap), FJ_ERR_CUDA. */
+fj_status fj_graph_lcc(fj_ctx* ctx, const fj_graph* g, fj_graph** out);
+
+/* ids[i] (HOST int32[n], n from fj_graph_stats) = the id in the parent graph
+ * of node i of a graph made by fj_graph_lcc, or i for an uploaded graph.
+ * Errors: FJ_ERR_ARG, FJ_ERR_CUDA. */
+fj_status fj_graph_node_ids(fj_ctx* ctx, const fj_graph* g, int32_t* ids);
+
 /* Size of a graph: nodes, stored off-diagonal CSR entries (2 x non-loop
  * edges), and whether it carries a weight array (0 = unit weights). */
 fj_status fj_graph_stats(const fj_graph* g, int64_t* n, int64_t* nnz,

@@ -18,7 +18,10 @@ can be checked against the paper by eye:
   disagreement, polarization, controversy, disagreement-controversy index),
   their quadratic forms (Proposition 1) and their l2-norm forms (Lemma PropA);
 * Algorithm 1 (APPROXIM) step by step, with Solve() realised by an FP64
-  conjugate-gradient solve.
+  conjugate-gradient solve;
+* the subgraph induced on the largest connected component, on which the
+  paper's experiments run (Sec. 5), with scipy's connected_components as the
+  component step.
 
 Readings of the paper used here (where it is silent or garbled):
 
@@ -116,6 +119,29 @@ def apply_laplacian(n, src, dst, w, x):
 def apply_i_plus_l(n, src, dst, w, x):
     """(I + L) x."""
     return np.asarray(x, dtype=np.float64) + apply_laplacian(n, src, dst, w, x)
+
+
+def largest_component(n, src, dst, w):
+    """The subgraph induced on the largest connected component (the paper's
+    experiments run on each network's largest connected component, Sec. 5):
+    its nodes in increasing id, and its edges (self-loops dropped) renumbered
+    to positions in that list, with their weights.  Of components of equal
+    size, the one holding the smallest node id wins.  Components come from
+    scipy's connected_components."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    src, dst, w = clean_edges(n, src, dst, w)
+    adj = coo_matrix((np.ones(src.shape[0]), (src, dst)), shape=(n, n))
+    ncomp, labels = connected_components(adj, directed=False)
+    sizes = np.bincount(labels, minlength=ncomp)
+    min_id = np.full(ncomp, n, dtype=np.int64)
+    np.minimum.at(min_id, labels, np.arange(n))
+    best = max(range(ncomp), key=lambda c: (sizes[c], -min_id[c]))
+    nodes = np.nonzero(labels == best)[0]
+    new = np.full(n, -1, dtype=np.int64)
+    new[nodes] = np.arange(nodes.shape[0])
+    keep = labels[src] == best
+    return nodes, new[src[keep]], new[dst[keep]], w[keep]
 
 
 # ------------------------------------------------------- the linear system

@@ -17,7 +17,8 @@
 
 #include "fj_internal.cuh"
 
-// defined in fj_graph.cu / fj_solve.cu
+// defined in fj_graph.cu, fj_solve.cu and fj_lcc.cu
+fj_status fj_lcc_device(const fj_graph* g, cudaStream_t st, fj_graph** out);
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m,
                                 const int32_t* src, const int32_t* dst, const float* w,
                                 bool merge_duplicates, fj_graph** out);
@@ -316,6 +317,35 @@ fj_status fj_graph_free(fj_ctx* c, fj_graph* g) {
   if (!g) return FJ_OK;
   FJ_CUDA(cudaSetDevice(c->device));
   return fj_free_graph_device(g, c->stream);
+}
+
+fj_status fj_graph_lcc(fj_ctx* c, const fj_graph* g, fj_graph** out) {
+  if (!c || !g || !out) {
+    set_error("fj_graph_lcc: ctx, graph and out must be non-NULL");
+    return FJ_ERR_ARG;
+  }
+  *out = nullptr;
+  if (g->device != c->device) {
+    set_error("fj_graph_lcc: graph belongs to device %d, context to %d", g->device, c->device);
+    return FJ_ERR_ARG;
+  }
+  FJ_CUDA(cudaSetDevice(c->device));
+  return fj_lcc_device(g, c->stream, out);
+}
+
+fj_status fj_graph_node_ids(fj_ctx* c, const fj_graph* g, int32_t* ids) {
+  if (!c || !g || !ids) {
+    set_error("fj_graph_node_ids: ctx, graph and ids must be non-NULL");
+    return FJ_ERR_ARG;
+  }
+  if (!g->orig_ids) {
+    for (int64_t i = 0; i < g->n; ++i) ids[i] = (int32_t)i;
+    return FJ_OK;
+  }
+  FJ_CUDA(cudaSetDevice(c->device));
+  FJ_CUDA(cudaMemcpyAsync(ids, g->orig_ids, (size_t)g->n * 4, cudaMemcpyDeviceToHost, c->stream));
+  FJ_CUDA(cudaStreamSynchronize(c->stream));
+  return FJ_OK;
 }
 
 fj_status fj_graph_stats(const fj_graph* g, int64_t* n, int64_t* nnz, int32_t* weighted) {

@@ -779,7 +779,7 @@ struct Pool {
 void fj_free_graph_arrays(fj_graph* g, cudaStream_t st) {
   void* arrays[] = {g->row_ptr,     g->col,       g->val,         g->dinv,      g->perm,
                     g->long_first,  g->chunk_row, g->chunk_begin, g->chunk_end, g->slice_off,
-                    g->sell_col,    g->sell_val,  g->unit_prefix};
+                    g->sell_col,    g->sell_val,  g->unit_prefix, g->orig_ids};
   for (void* p : arrays)
     if (p) cudaFreeAsync(p, st);
 }

@@ -63,6 +63,7 @@ struct fj_graph {
   float* val;
   float* dinv;
   int32_t* perm;  // perm[i] = input id of solver node i
+  int32_t* orig_ids;  // for an extracted component: node id in the parent graph (else null)
   // long rows [0, n_long) in chunks; rows [n_nz, n) have no entries
   int64_t n_long;
   int64_t n_nz;

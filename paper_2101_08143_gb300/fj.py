@@ -81,6 +81,8 @@ _SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int32)]),
     "fj_solve_ex": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P,
                                      ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
+    "fj_graph_lcc": (ctypes.c_int32, [_P, _P, ctypes.POINTER(_P)]),
+    "fj_graph_node_ids": (ctypes.c_int32, [_P, _P, _P]),
     "fj_solve_warm": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, _P,
                                        ctypes.POINTER(Opts), ctypes.POINTER(Info)]),
     "fj_solve": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P,
@@ -152,6 +154,19 @@ class Graph:
         _check(load().fj_graph_stats(self.handle, ctypes.byref(n), ctypes.byref(nnz),
                                      ctypes.byref(wt)), "fj_graph_stats")
         return {"n": n.value, "nnz": nnz.value, "weighted": bool(wt.value)}
+
+    def lcc(self) -> "Graph":
+        """The subgraph induced on the largest connected component."""
+        h = _P()
+        _check(load().fj_graph_lcc(self.ctx.handle, self.handle, ctypes.byref(h)), "fj_graph_lcc")
+        return Graph(self.ctx, h)
+
+    def node_ids(self) -> np.ndarray:
+        """Node i's id in the parent graph (i for an uploaded graph)."""
+        ids = np.empty(self.stats()["n"], dtype=np.int32)
+        _check(load().fj_graph_node_ids(self.ctx.handle, self.handle, _P(ids.ctypes.data)),
+               "fj_graph_node_ids")
+        return ids
 
     def free(self):
         if self.handle:

@@ -36,6 +36,13 @@ def _check_quantities(gq, oq, s, rtol):
         assert err <= rtol, (name, gq[name], oq[name], err)
 
 
+def _oracle_edges(n, src, dst, w, s, tol=1e-12):
+    s = np.asarray(s, dtype=np.float64).reshape(n, -1)
+    z = fo.solve(n, src, dst, w, s, tol=tol).reshape(n, -1)
+    q = [fo.quantities_from_z(n, src, dst, w, s[:, j], z[:, j]) for j in range(s.shape[1])]
+    return z, q
+
+
 def _oracle(g, s, tol=1e-12):
     s = np.asarray(s, dtype=np.float64).reshape(g.n, -1)
     z = fo.solve(g.n, g.src, g.dst, g.w, s, tol=tol).reshape(g.n, -1)
@@ -227,6 +234,48 @@ def test_warm_start(ctx, k, two):
         for qq in (qw, qp, qc):
             _check_quantities(qq[j], qo[j], s2[:, j], 1e-6)
     np.testing.assert_allclose(zw, zo, atol=1e-8)
+
+
+@pytest.mark.parametrize("weighted,merge", [(True, False), (False, False), (True, True)])
+def test_largest_connected_component(ctx, weighted, merge):
+    """fj_graph_lcc: the component's nodes (in increasing input id) match the
+    oracle's, and solving on it matches the oracle on the induced subgraph;
+    a graph of several components, isolated nodes and a hub row of several
+    chunks.  With merge, a repeated pair survives as a parallel edge."""
+    a = synth.chung_lu(9000, 40_000, 2.1, seed=51, weighted=weighted)
+    b = synth.erdos_renyi(3000, 9000, seed=52, weighted=weighted)
+    n = a.n + b.n + 500  # 500 isolated nodes
+    rng = np.random.default_rng(5)
+    relabel = rng.permutation(n)
+    src = relabel[np.concatenate([a.src, b.src + a.n])].astype(np.int32)
+    dst = relabel[np.concatenate([a.dst, b.dst + a.n])].astype(np.int32)
+    w = np.concatenate([a.w, b.w]) if weighted else None
+    if merge:
+        src, dst = np.append(src, dst[0]), np.append(dst, src[0])
+        w = np.append(w, np.float32(0.25)) if weighted else None
+    nodes, s2, d2, w2 = fo.largest_component(n, src, dst, w)
+    assert len(nodes) < a.n + 1
+    s = synth.opinions_uniform(n, 2, 9)
+    sl = s[nodes]
+    zo, qo = _oracle_edges(len(nodes), s2, d2, w2, sl)
+    with ctx.upload(n, src, dst, w, merge_duplicates=merge) as dg:
+        with dg.lcc() as lg:
+            st = lg.stats()
+            assert st["n"] == len(nodes) and st["nnz"] == 2 * len(s2) and st["weighted"] == weighted
+            np.testing.assert_array_equal(lg.node_ids(), nodes)
+            z, q, _ = ctx.solve(lg, sl)
+        np.testing.assert_array_equal(dg.node_ids(), np.arange(n))
+    for j in range(2):
+        _check_quantities(q[j], qo[j], sl[:, j], 1e-6)
+    np.testing.assert_allclose(z, zo, atol=1e-8)
+
+
+def test_lcc_of_an_edgeless_graph_is_node_zero(ctx):
+    g = synth.edgeless(50)
+    with ctx.upload_edges(g) as dg:
+        with dg.lcc() as lg:
+            assert lg.stats()["n"] == 1 and lg.stats()["nnz"] == 0
+            assert list(lg.node_ids()) == [0]
 
 
 def test_two_solves_mode_rejected_where_unsupported(ctx):

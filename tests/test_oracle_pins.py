@@ -393,3 +393,56 @@ def test_planted_mistakes_are_caught(monkeypatch):
     assert not pins_pass()
     monkeypatch.undo()
     assert pins_pass()
+
+
+# ------------------------------------------------- largest connected component
+
+def _bfs_components(n, src, dst):
+    adj = [[] for _ in range(n)]
+    for a, b in zip(src, dst):
+        if a != b:
+            adj[a].append(b)
+            adj[b].append(a)
+    comp = [-1] * n
+    comps = []
+    for v in range(n):
+        if comp[v] >= 0:
+            continue
+        comp[v] = len(comps)
+        stack, members = [v], [v]
+        while stack:
+            x = stack.pop()
+            for y in adj[x]:
+                if comp[y] < 0:
+                    comp[y] = comp[v]
+                    stack.append(y)
+                    members.append(y)
+        comps.append(sorted(members))
+    return comps
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_largest_component_matches_breadth_first_search(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(5, 60))
+    m = int(rng.integers(0, 2 * n))
+    src = rng.integers(0, n, m)
+    dst = rng.integers(0, n, m)
+    w = rng.uniform(0.1, 1.0, m).astype(np.float32)
+    comps = _bfs_components(n, src, dst)
+    want = max(comps, key=lambda c: (len(c), -c[0]))
+    nodes, s2, d2, w2 = fo.largest_component(n, src, dst, w)
+    assert list(nodes) == want
+    pos = {v: i for i, v in enumerate(want)}
+    exp = sorted((pos[a], pos[b], float(x)) for a, b, x in zip(src, dst, w)
+                 if a != b and a in pos)
+    assert sorted(zip(s2.tolist(), d2.tolist(), w2.tolist())) == exp
+
+
+def test_largest_component_ties_go_to_the_smallest_id():
+    # two triangles {1,2,3} and {0,4,5}, one isolated node 6
+    src = np.array([1, 2, 3, 4, 5, 0])
+    dst = np.array([2, 3, 1, 5, 0, 4])
+    nodes, s2, d2, _ = fo.largest_component(7, src, dst, None)
+    assert list(nodes) == [0, 4, 5]
+    assert sorted(zip(s2, d2)) == [(0, 1), (1, 2), (2, 0)]
