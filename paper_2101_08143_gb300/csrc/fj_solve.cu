@@ -14,9 +14,10 @@
 //
 // The inner solver is the Chronopoulos-Gear form of preconditioned CG: both
 // inner products of an iteration come out of one grid-wide reduction, so an
-// iteration costs two grid barriers (vector update | SpMV walk).  The SpMV
-// reduction (w, u) is taken as u^T u + 1/2 sum_CSR w (u_i - u_j)^2, which the
-// merge-path walk produces without waiting for split rows to be combined.
+// iteration costs two grid barriers (vector update | SpMV walk; a third for
+// the 8-32 column walks, whose work-unit sums are added after the walk).  The
+// SpMV reduction (w, u) is taken as u^T u + 1/2 sum_CSR w (u_i - u_j)^2,
+// which the walks produce without waiting for split rows to be combined.
 //
 // All reductions are two-level and in a fixed order (per block, then over
 // blocks), and every block evaluates the same scalars, so control flow is
@@ -247,7 +248,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   const int64_t gtid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * kThreads;
   const int c = threadIdx.x % K;
-  const int64_t wg = (int64_t)blockIdx.x * kWarps + warp;
   // per-warp staging of the wide walks' row values
   VI* my_sxr = reinterpret_cast<VI*>(smem_raw + warp * kWideStageBytes);
   df64* my_sxr64 = reinterpret_cast<df64*>(my_sxr);
@@ -256,7 +256,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   unsigned epoch = 0;  // barriers passed (used by thread 0)
   // every K walks the same work units (sliced ELL for K <= 4, lanes as
   // columns for K >= 8), so all row sums are complete after a walk
-  constexpr bool kSell = true;
   constexpr bool kWide = K >= 8;
 
   // K <= 4: this warp's share of the work units, split by cost;
@@ -465,19 +464,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       // (u, (I+L) u).
       {
         double qv;
-        if constexpr (kSell) {
-          if constexpr (kWide) {
-            wide_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.unit_counter, unit_base, P.quad_u, my_sxr);
-            unit_base += unit_step;
-            if (!grid_sync(P.bar, status, epoch)) return;
-            qv = unit_sum<K>(P.quad_u, u0, u1);
-          } else {
-            VI quad[K];
+        if constexpr (kWide) {
+          wide_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.unit_counter, unit_base, P.quad_u, my_sxr);
+          unit_base += unit_step;
+          if (!grid_sync(P.bar, status, epoch)) return;
+          qv = unit_sum<K>(P.quad_u, u0, u1);
+        } else {
+          VI quad[K];
 #pragma unroll
-            for (int cc = 0; cc < K; ++cc) quad[cc] = VI(0);
-            sell_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, u0, u1, quad);
-            qv = lane_share<VI, K>(quad);
-          }
+          for (int cc = 0; cc < K; ++cc) quad[cc] = VI(0);
+          sell_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, u0, u1, quad);
+          qv = lane_share<VI, K>(quad);
         }
         const double v[1] = {qv};
         const int sl[1] = {S_EQ};
