@@ -320,18 +320,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
     return grid_sync(P.bar, status, epoch);
   };
 
-  // warm start: q = z0 - mu 1, and its residual walk
+  // warm start: q = z0 - mu 1 (its residual walk opens the loop)
   const bool warm = P.z0 != nullptr;
   if (warm) {
     for (int64_t idx = gtid; idx < NK; idx += gstride)
       P.q[idx] = df_from_double(P.z0[(int64_t)(c >> P.col_shift) * P.ld + P.perm[idx / K]] - mu[c]);
     if (!grid_sync(P.bar, status, epoch)) return;
-    if (!residual_walk()) return;
   }
 
   int iters = 0, refines = 0;
   bool init = true;
+  bool need_walk = warm;  // q changed since the last residual walk
   while (true) {
+    if (need_walk && !residual_walk()) return;
     // ------------------------------------------------ float64 residual pass
     // r64 = s_bar - q - t64 (t64 = off-diagonal part of L q, from the walk)
     // plus the quantity partials and the start of the next inner solve.
@@ -613,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         P.q[idx] = df_add(P.q[idx], df_from_double((double)P.x[idx]));
     }
     if (!grid_sync(P.bar, status, epoch)) return;
-    if (!residual_walk()) return;
+    need_walk = true;
   }
 
   // ---------------------------------------------------------------- output
