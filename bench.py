@@ -517,6 +517,10 @@ def main():
                            "note": "resident graph, solve + quantities + z"},
             "iterations": {"inner": iters, "refinements": refines,
                            "rel_residual": max(i["rel_residual"] for i in infos)},
+            # nnz x k x inner iterations per second of the solve kernel, and
+            # per second of the whole step
+            "edge_iterations_per_s": {"kernel": nnz * k * iters / (kern_ms / 1000.0),
+                                      "step": nnz * k * iters * value / k},
             "roofline": {"kernel": "k_solve<float,1>", "bound": "hbm", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": f"{peak_kind} (hbm_gbs, burst copy)",
