@@ -21,7 +21,8 @@
 fj_status fj_lcc_device(const fj_graph* g, cudaStream_t st, fj_graph** out);
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m,
                                 const int32_t* src, const int32_t* dst, const float* w,
-                                bool merge_duplicates, fj_graph** out);
+                                bool merge_duplicates, fj_graph** out, int32_t* copy_src = nullptr, int32_t* copy_dst = nullptr,
+                                float* copy_w = nullptr);
 fj_status fj_free_graph_device(fj_graph* g, cudaStream_t st);
 size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms);
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k,
@@ -141,6 +142,17 @@ fj_status grow(void** p, size_t* have, size_t need) {
   }
   *have = sz;
   return FJ_OK;
+}
+
+// Device address of a page-locked (registered) host array, or null for
+// memory a kernel cannot read directly.
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
 }
 
 // Launch widths for k columns: 32 at a time, then 16, 8, 4, 2, 1.
@@ -295,13 +307,24 @@ fj_status fj_graph_upload(fj_ctx* c, int64_t n, int64_t m, const int32_t* src, c
     return FJ_ERR_OOM;
   }
   fj_status rc = FJ_OK;
-  if (m > 0) {
-    cudaError_t e = cudaMemcpyAsync(ds, src, m * 4, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dd, dst, m * 4, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess && w) e = cudaMemcpyAsync(dw, w, m * 4, cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) rc = cuda_fail(e, "fj_graph_upload copy");
+  // Page-locked (registered) host arrays are read by the validation pass
+  // itself, which writes the device copy on the way; other host memory is
+  // copied first.
+  const void* ms = mapped_host(src);
+  const void* md = mapped_host(dst);
+  const void* mw = w ? mapped_host(w) : nullptr;
+  if (m > 0 && ms && md && (!w || mw)) {
+    rc = fj_build_graph_device(c->device, c->stream, n, m, (const int32_t*)ms, (const int32_t*)md,
+                               (const float*)mw, merge, out, ds, dd, dw);
+  } else {
+    if (m > 0) {
+      cudaError_t e = cudaMemcpyAsync(ds, src, m * 4, cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dd, dst, m * 4, cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess && w) e = cudaMemcpyAsync(dw, w, m * 4, cudaMemcpyHostToDevice, c->stream);
+      if (e != cudaSuccess) rc = cuda_fail(e, "fj_graph_upload copy");
+    }
+    if (rc == FJ_OK) rc = fj_build_graph_device(c->device, c->stream, n, m, ds, dd, w ? dw : nullptr, merge, out);
   }
-  if (rc == FJ_OK) rc = fj_build_graph_device(c->device, c->stream, n, m, ds, dd, w ? dw : nullptr, merge, out);
   cudaFreeAsync(ds, c->stream);
   cudaFreeAsync(dd, c->stream);
   if (dw) cudaFreeAsync(dw, c->stream);

@@ -38,16 +38,25 @@ constexpr int64_t kScanDirectTiles = 1024;
 
 // ------------------------------------------------------------ validation
 
+// csrc/cdst/cw (nullable): the edge list is read from mapped host memory
+// and copied to these device arrays on the way.
 __global__ void k_validate_degree(int64_t m, int64_t n, const int32_t* __restrict__ src,
                                   const int32_t* __restrict__ dst, const float* __restrict__ w,
-                                  int64_t* __restrict__ err, int32_t* __restrict__ deg) {
+                                  int64_t* __restrict__ err, int32_t* __restrict__ deg,
+                                  int32_t* __restrict__ csrc, int32_t* __restrict__ cdst,
+                                  float* __restrict__ cw) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t u = src[e], v = dst[e];
+    const float x = w ? w[e] : 1.0f;
+    if (csrc) {
+      csrc[e] = u;
+      cdst[e] = v;
+      if (w) cw[e] = x;
+    }
     int bad = 0;
     if (u < 0 || u >= n || v < 0 || v >= n) bad |= kErrBadId;
     if (w) {
-      const float x = w[e];
       if (!(x > 0.0f) || isinf(x)) bad |= kErrBadWeight;
     }
     if (bad) {
@@ -787,7 +796,8 @@ void fj_free_graph_arrays(fj_graph* g, cudaStream_t st) {
 // Called by the C ABI (fj_api.cpp).  src/dst/w are device pointers.
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m,
                                 const int32_t* src, const int32_t* dst, const float* w,
-                                bool merge_duplicates, fj_graph** out) {
+                                bool merge_duplicates, fj_graph** out, int32_t* copy_src,
+                                int32_t* copy_dst, float* copy_w) {
   const int64_t N = 2 * m;
   const bool weighted = (w != nullptr);
   Pool pool(st);
@@ -807,8 +817,14 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   // ---- 1. validation and degrees
   if (m > 0) {
     count_launches(1);
-    k_validate_degree<<<grid_for(m, 256), 256, 0, st>>>(m, n, src, dst, w, dcnt + 6, deg);
+    k_validate_degree<<<grid_for(m, 256), 256, 0, st>>>(m, n, src, dst, w, dcnt + 6, deg, copy_src, copy_dst,
+                                                         copy_w);
     FJ_CUDA(cudaGetLastError());
+  }
+  if (copy_src) {  // later passes read the device copy
+    src = copy_src;
+    dst = copy_dst;
+    if (w) w = copy_w;
   }
 
   // ---- 2. solver order: stable sort of nodes by decreasing degree

@@ -20,7 +20,8 @@
 #include "fj_internal.cuh"
 
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m, const int32_t* src,
-                                const int32_t* dst, const float* w, bool merge_duplicates, fj_graph** out);
+                                const int32_t* dst, const float* w, bool merge_duplicates, fj_graph** out, int32_t* copy_src = nullptr, int32_t* copy_dst = nullptr,
+                                float* copy_w = nullptr);
 
 namespace fj {
 namespace {

@@ -29,7 +29,8 @@
 #include "fj_internal.cuh"
 
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m, const int32_t* src,
-                                const int32_t* dst, const float* w, bool merge_duplicates, fj_graph** out);
+                                const int32_t* dst, const float* w, bool merge_duplicates, fj_graph** out, int32_t* copy_src = nullptr, int32_t* copy_dst = nullptr,
+                                float* copy_w = nullptr);
 void fj_free_graph_arrays(fj_graph* g, cudaStream_t st);
 size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms);
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k, const double* s, double* z,

@@ -278,6 +278,40 @@ def test_lcc_of_an_edgeless_graph_is_node_zero(ctx):
             assert list(lg.node_ids()) == [0]
 
 
+def test_page_locked_host_edges(ctx):
+    """Page-locked host edge arrays are read by the validation pass directly
+    (mapped), pageable ones copied first: both give the same bits as a
+    device-pointer upload, and bad edges are still rejected."""
+    import torch
+    from paper_2101_08143_gb300 import fj
+    g = synth.chung_lu(30_000, 150_000, 2.2, seed=61, weighted=True)
+    s = synth.opinions_uniform(g.n, 1, 4)[:, 0]
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    dev = torch.device("cuda")
+    with ctx.upload(g.n, torch.from_numpy(g.src).to(dev), torch.from_numpy(g.dst).to(dev),
+                    torch.from_numpy(g.w).to(dev)) as dg:
+        z0, q0, _ = ctx.solve(dg, s)
+    for src, dst, w in ((pin(g.src), pin(g.dst), pin(g.w)), (pin(g.src), g.dst, pin(g.w)),
+                        (pin(g.src), pin(g.dst), None)):
+        with ctx.upload(g.n, src, dst, w) as dg:
+            z, q, _ = ctx.solve(dg, s)
+        if w is not None:
+            assert np.array_equal(z, z0) and q == q0
+        else:
+            zo, qo = _oracle_edges(g.n, g.src, g.dst, None, s)
+            _check_quantities(q[0], qo[0], s, 1e-6)
+    bad = pin(g.dst.copy())
+    bad[1234] = g.n + 7
+    with pytest.raises(fj.FJError) as e:
+        ctx.upload(g.n, pin(g.src), bad, pin(g.w))
+    assert e.value.code == fj.FJ_ERR_GRAPH and "edge 1234" in str(e.value)
+    badw = pin(g.w.copy())
+    badw[99] = -1.0
+    with pytest.raises(fj.FJError) as e:
+        ctx.upload(g.n, pin(g.src), pin(g.dst), badw)
+    assert e.value.code == fj.FJ_ERR_GRAPH and "edge 99" in str(e.value)
+
+
 def test_two_solves_mode_rejected_where_unsupported(ctx):
     from paper_2101_08143_gb300 import fj
     g = synth.erdos_renyi(500, 2000, seed=4)
