@@ -69,3 +69,15 @@ def test_serving_arguments_rejected_without_a_device():
     assert lib.fj_submit(None, None, 1, None, None, C.byref(t)) == fj.FJ_ERR_ARG
     assert lib.fj_poll(None, 1, 0, None, None) == fj.FJ_ERR_ARG
     assert lib.fj_serve_config(None, 1, 0, 0) == fj.FJ_ERR_ARG
+
+
+def test_new_entry_points_reject_null_arguments_without_a_device():
+    import ctypes as C
+    lib = fj.load()
+    out = C.c_void_p()
+    assert lib.fj_graph_lcc(None, None, C.byref(out)) == fj.FJ_ERR_ARG
+    assert b"non-NULL" in lib.fj_last_error()
+    assert lib.fj_graph_node_ids(None, None, None) == fj.FJ_ERR_ARG
+    info = fj.Info()
+    assert lib.fj_solve_warm(None, None, 1, None, None, None, None, None, C.byref(info)) == fj.FJ_ERR_ARG
+    assert b"z0" in lib.fj_last_error()
