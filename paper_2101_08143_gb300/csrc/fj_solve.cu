@@ -257,6 +257,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   // every K walks the same work units (sliced ELL for K <= 4, lanes as
   // columns for K >= 8), so all row sums are complete after a walk
   constexpr bool kWide = K >= 8;
+  // narrow walks: entries in flight per lane (8 for rows of up to 8 bytes in
+  // the float32-inner kernels; 4 otherwise, which keeps the float64-inner
+  // kernels from spilling)
+  constexpr int kInnerBatch = (sizeof(VI) == 4 && K <= 2) ? 8 : 4;
+  constexpr int kResidBatch = (sizeof(VI) == 4 && K == 1) ? 8 : 4;
 
   // K <= 4: this warp's share of the work units, split by cost;
   // K >= 8: the units whose edge sums this block adds up (even split)
@@ -311,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       df64 qd[K];
 #pragma unroll
       for (int cc = 0; cc < K; ++cc) qd[cc] = df_from_float(0.0f);
-      sell_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, u0, u1, qd);
+      sell_walk<df64, K, kResidBatch>(P.sg, P.q, P.t64, P.hub_part64, u0, u1, qd);
       quad = lane_share<df64, K>(qd);
     }
     const double v[1] = {quad};
@@ -474,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
           VI quad[K];
 #pragma unroll
           for (int cc = 0; cc < K; ++cc) quad[cc] = VI(0);
-          sell_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, u0, u1, quad);
+          sell_walk<VI, K, kInnerBatch>(P.sg, P.u, P.t, P.hub_part, u0, u1, quad);
           qv = lane_share<VI, K>(quad);
         }
         const double v[1] = {qv};

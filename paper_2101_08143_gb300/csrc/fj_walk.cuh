@@ -105,13 +105,12 @@ __device__ __forceinline__ int64_t sell_unit_start(const SellGraph& g, int64_t w
 
 // out[r*K+c] = sum_j w_rj (x[r*K+c] - x[j*K+c]) for every row of units
 // [u0, u1); quad[c] accumulates this lane's share of sum w (x_r - x_j)^2.
-template <typename T, int K>
+template <typename T, int K, int kB>
 __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
                                           T* __restrict__ part, int64_t u0,
                                           int64_t u1, T (&quad)[K]) {
   const int lane = threadIdx.x & 31;
-  // entries in flight per lane between two dependent round trips
-  constexpr int kB = (K * sizeof(T) <= 4) ? 8 : 4;
+  // kB: entries in flight per lane between two dependent round trips
   // bounds of unit u: a chunk's row and entry range, or a slice's offsets;
   // those of the next unit are loaded while the current one runs
   auto bounds = [&](int64_t u, int32_t& r, int64_t& lo, int64_t& hi) {
