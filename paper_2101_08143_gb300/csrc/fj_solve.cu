@@ -34,6 +34,7 @@ namespace fj {
 constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
 constexpr int kMaxBlocksPerSM = 4;
+constexpr int kMaxDevices = 64;
 constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s per barrier wait
 
 enum Slot {
@@ -647,9 +648,25 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   const size_t red_bytes = (size_t)7 * kWarps * K * sizeof(double);
   const size_t stage = (K <= 4) ? 0 : (size_t)kWarps * kWideStageBytes;
   const size_t dyn = std::max(red_bytes, stage);
-  FJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  // the attribute and the occupancy query once per device and instantiation
+  static std::mutex setup_mu;
+  static int per_sm_of[kMaxDevices] = {};
+  int device = 0;
+  FJ_CUDA(cudaGetDevice(&device));
+  if (device < 0 || device >= kMaxDevices) {
+    set_error("device %d out of range", device);
+    return FJ_ERR_ARG;
+  }
   int per_sm = 0;
-  FJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, dyn));
+  {
+    std::lock_guard<std::mutex> lock(setup_mu);
+    if (per_sm_of[device] == 0) {
+      FJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+      FJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, dyn));
+      per_sm_of[device] = per_sm > 0 ? per_sm : -1;
+    }
+    per_sm = per_sm_of[device];
+  }
   if (per_sm < 1) {
     set_error("solver kernel does not fit on an SM");
     return FJ_ERR_CUDA;
