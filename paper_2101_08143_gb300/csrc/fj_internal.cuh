@@ -32,8 +32,11 @@ constexpr int kPad = 64;
 // processed warp-wide in chunks of at most kChunkLen entries.
 constexpr int kSellMaxLen = 64;
 constexpr int kChunkLen = 512;
-// Degree keys of the reordering sort saturate here (11-bit keys).
-constexpr int kDegKeyMax = 2047;
+// Degree keys of the reordering sort saturate here (8-bit keys: one radix
+// pass).  Rows of more than kSellMaxLen entries come first either way, and
+// shorter rows are fully ordered by length; rows of degree >= kDegKeyMax
+// keep their input order among themselves.
+constexpr int kDegKeyMax = 255;
 
 // Error bits raised by device code.
 enum : int {
