@@ -108,29 +108,11 @@ __device__ __forceinline__ float mul_w(float d, float w) { return w * d; }
 __device__ __forceinline__ double mul_w(double d, float w) { return (double)w * d; }
 __device__ __forceinline__ df64 mul_w(df64 d, float w) { return df_mul_f(d, w); }
 
-// Warp shuffles for every value type of the walks.
-__device__ __forceinline__ float shfl_up_v(float v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
-__device__ __forceinline__ double shfl_up_v(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
-__device__ __forceinline__ df64 shfl_up_v(df64 v, int d) {
-  return df_make(__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d));
-}
-__device__ __forceinline__ float shfl_v(float v, int l) { return __shfl_sync(0xffffffffu, v, l); }
-__device__ __forceinline__ double shfl_v(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
-__device__ __forceinline__ df64 shfl_v(df64 v, int l) {
-  return df_make(__shfl_sync(0xffffffffu, v.hi, l), __shfl_sync(0xffffffffu, v.lo, l));
-}
+// Warp xor-shuffle for every value type of the walks.
 __device__ __forceinline__ float shfl_xor_v(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 __device__ __forceinline__ double shfl_xor_v(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 __device__ __forceinline__ df64 shfl_xor_v(df64 v, int m) {
   return df_make(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
-}
-
-// L2-only load (data written by other blocks of the same launch).
-__device__ __forceinline__ float ldcg_v(const float* p) { return __ldcg(p); }
-__device__ __forceinline__ double ldcg_v(const double* p) { return __ldcg(p); }
-__device__ __forceinline__ df64 ldcg_v(const df64* p) {
-  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
-  return df_make(v.x, v.y);
 }
 
 }  // namespace fj

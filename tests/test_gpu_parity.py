@@ -312,6 +312,35 @@ def test_page_locked_host_edges(ctx):
     assert e.value.code == fj.FJ_ERR_GRAPH and "edge 99" in str(e.value)
 
 
+def test_lcc_tie_goes_to_the_smallest_id(ctx):
+    src = np.array([1, 2, 3, 4, 5, 0], np.int32)
+    dst = np.array([2, 3, 1, 5, 0, 4], np.int32)
+    with ctx.upload(7, src, dst) as dg:
+        with dg.lcc() as lg:
+            assert list(lg.node_ids()) == [0, 4, 5]
+            assert lg.stats()["nnz"] == 6
+
+
+def test_two_solves_and_warm_start_with_device_pointers(ctx):
+    """Both modes through device-resident s, z and z0."""
+    import torch
+    from paper_2101_08143_gb300 import fj
+    g = synth.chung_lu(10_000, 50_000, 2.2, seed=71, weighted=True)
+    s = synth.opinions_uniform(g.n, 3, 5)
+    zo, qo = _oracle(g, s)
+    dev = torch.device("cuda")
+    sd = torch.from_numpy(np.ascontiguousarray(s.T)).to(dev)
+    with ctx.upload_edges(g) as dg:
+        z2, q2, _ = ctx.solve(dg, sd, opts=fj.default_opts(tol=1e-10, flags=fj.FJ_TWO_SOLVES))
+        zw, qw, info = ctx.solve(dg, sd, opts=fj.default_opts(tol=1e-10), z0=z2)
+    assert info["iterations"] == 0
+    for j in range(3):
+        _check_quantities(q2[j], qo[j], s[:, j], 1e-6)
+        _check_quantities(qw[j], qo[j], s[:, j], 1e-6)
+    np.testing.assert_allclose(z2.cpu().numpy().T, zo, atol=1e-8)
+    np.testing.assert_allclose(zw.cpu().numpy().T, zo, atol=1e-8)
+
+
 def test_two_solves_mode_rejected_where_unsupported(ctx):
     from paper_2101_08143_gb300 import fj
     g = synth.erdos_renyi(500, 2000, seed=4)
