@@ -85,12 +85,20 @@ __global__ void k_cc_jump(int32_t* __restrict__ parent, int64_t n, int* __restri
   if (more) *deeper = 1;
 }
 
-// Per root: size and smallest input id of its component.
+// Per root: size and smallest input id of its component.  Most nodes share
+// one root (the large component), so the lanes of a warp with equal roots
+// combine first: one atomic per distinct root and warp.
 __global__ void k_cc_sizes(const int32_t* __restrict__ parent, const int32_t* __restrict__ perm, int64_t n,
                            int32_t* __restrict__ size, int32_t* __restrict__ min_in) {
+  const int lane = threadIdx.x & 31;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    atomicAdd(&size[parent[i]], 1);
-    atomicMin(&min_in[parent[i]], perm[i]);
+    const int32_t r = parent[i];
+    const unsigned peers = __match_any_sync(__activemask(), r);
+    const unsigned lo = __reduce_min_sync(peers, (unsigned)perm[i]);
+    if (lane == __ffs(peers) - 1) {
+      atomicAdd(&size[r], __popc(peers));
+      atomicMin(&min_in[r], (int32_t)lo);
+    }
   }
 }
 
@@ -157,46 +165,49 @@ __global__ void k_tile_number(const int32_t* __restrict__ keep, int64_t n, const
 }
 
 // Edge list of the component: every CSR entry (i, j) with i < j of a kept
-// node, in CSR order.  Pass 1 counts per row (a warp per long row, a thread
-// per short row); pass 2 writes at the row's scanned offset.
+// node, in CSR order.  The units are the chunks of the long rows (a warp
+// each), then the short rows [n_long, n) (a thread each): pass 1 counts per
+// unit, pass 2 writes at the unit's scanned offset.
 __device__ __forceinline__ bool take(const int32_t* parent, int32_t root, int32_t i, int32_t j) {
   return j > i && parent[i] == root;
 }
 
 __global__ void k_lcc_count(const fj_graph g, const int32_t* __restrict__ parent, int32_t root,
-                            int64_t* __restrict__ row_cnt) {
+                            int64_t* __restrict__ unit_cnt) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
-  for (int64_t r = tid >> 5; r < g.n_long; r += nthreads >> 5) {
+  for (int64_t ch = tid >> 5; ch < g.n_chunks; ch += nthreads >> 5) {
+    const int32_t r = g.chunk_row[ch], e = g.chunk_end[ch];
     int64_t c = 0;
-    for (int32_t p0 = g.row_ptr[r]; p0 < g.row_ptr[r + 1]; p0 += 32) {
+    for (int32_t p0 = g.chunk_begin[ch]; p0 < e; p0 += 32) {
       const int32_t p = p0 + lane;
-      const bool t = p < g.row_ptr[r + 1] && take(parent, root, (int32_t)r, g.col[p]);
+      const bool t = p < e && take(parent, root, r, g.col[p]);
       c += __popc(__ballot_sync(kFullMask, t));
     }
-    if (lane == 0) row_cnt[r] = c;
+    if (lane == 0) unit_cnt[ch] = c;
   }
   for (int64_t r = g.n_long + tid; r < g.n; r += nthreads) {
     int64_t c = 0;
     if (r < g.n_nz)
       for (int32_t p = g.row_ptr[r]; p < g.row_ptr[r + 1]; ++p) c += take(parent, root, (int32_t)r, g.col[p]);
-    row_cnt[r] = c;
+    unit_cnt[g.n_chunks + r - g.n_long] = c;
   }
 }
 
 __global__ void k_lcc_write(const fj_graph g, const int32_t* __restrict__ parent, int32_t root,
-                            const int64_t* __restrict__ row_off, const int32_t* __restrict__ new_id,
+                            const int64_t* __restrict__ unit_off, const int32_t* __restrict__ new_id,
                             int32_t* __restrict__ src, int32_t* __restrict__ dst, float* __restrict__ w) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
-  for (int64_t r = tid >> 5; r < g.n_long; r += nthreads >> 5) {
-    int64_t o = row_off[r];
+  for (int64_t ch = tid >> 5; ch < g.n_chunks; ch += nthreads >> 5) {
+    const int32_t r = g.chunk_row[ch], e = g.chunk_end[ch];
+    int64_t o = unit_off[ch];
     const int32_t a = new_id[g.perm[r]];
-    for (int32_t p0 = g.row_ptr[r]; p0 < g.row_ptr[r + 1]; p0 += 32) {
+    for (int32_t p0 = g.chunk_begin[ch]; p0 < e; p0 += 32) {
       const int32_t p = p0 + lane;
-      const bool t = p < g.row_ptr[r + 1] && take(parent, root, (int32_t)r, g.col[p]);
+      const bool t = p < e && take(parent, root, r, g.col[p]);
       const unsigned bal = __ballot_sync(kFullMask, t);
       if (t) {
         const int64_t q = o + __popc(bal & ((1u << lane) - 1u));
@@ -208,7 +219,7 @@ __global__ void k_lcc_write(const fj_graph g, const int32_t* __restrict__ parent
     }
   }
   for (int64_t r = g.n_long + tid; r < g.n_nz; r += nthreads) {
-    int64_t o = row_off[r];
+    int64_t o = unit_off[g.n_chunks + r - g.n_long];
     const int32_t a = new_id[g.perm[r]];
     for (int32_t p = g.row_ptr[r]; p < g.row_ptr[r + 1]; ++p) {
       const int32_t j = g.col[p];
@@ -293,8 +304,9 @@ fj_status fj_lcc_device(const fj_graph* g, cudaStream_t st, fj_graph** out) {
       malloc_async(&min_in, n * 4, st) != cudaSuccess || malloc_async(&keep, n * 4, st) != cudaSuccess ||
       malloc_async(&new_id, n * 4, st) != cudaSuccess || malloc_async(&ids, n * 4, st) != cudaSuccess ||
       malloc_async(&tile32, tiles * 4, st) != cudaSuccess || malloc_async(&flags, 16, st) != cudaSuccess ||
-      malloc_async(&best, 8, st) != cudaSuccess || malloc_async(&row_cnt, n * 8, st) != cudaSuccess ||
-      malloc_async(&row_off, n * 8, st) != cudaSuccess || malloc_async(&tile64, tiles * 8, st) != cudaSuccess ||
+      malloc_async(&best, 8, st) != cudaSuccess || malloc_async(&row_cnt, (n + g->n_chunks) * 8, st) != cudaSuccess ||
+      malloc_async(&row_off, (n + g->n_chunks) * 8, st) != cudaSuccess ||
+      malloc_async(&tile64, (tiles + g->n_chunks / kTile + 1) * 8, st) != cudaSuccess ||
       malloc_async(&total, 8, st) != cudaSuccess) {
     cudaGetLastError();
     if (ids) cudaFreeAsync(ids, st);
@@ -349,10 +361,12 @@ fj_status fj_lcc_device(const fj_graph* g, cudaStream_t st, fj_graph** out) {
   FJ_CUDA(cudaMemcpyAsync(&root, flags + 2, 4, cudaMemcpyDeviceToHost, st));
   FJ_CUDA(cudaStreamSynchronize(st));
   const int64_t n_lcc = (int64_t)(hbest >> 32);
+  const int64_t units = g->n_chunks + (n - g->n_long);
+  const int64_t utiles = (units + kTile - 1) / kTile;
   count_launches(3);
-  k_lcc_count<<<grid_of(std::max<int64_t>(g->n_long * 32, n), 256), 256, 0, st>>>(*g, parent, root, row_cnt);
-  k_row_tiles<<<(unsigned)tiles, kTile, 0, st>>>(row_cnt, n, tile64);
-  k_row_offsets<<<(unsigned)tiles, kTile, 0, st>>>(row_cnt, n, tile64, row_off, total);
+  k_lcc_count<<<grid_of(std::max<int64_t>(g->n_chunks * 32, n), 256), 256, 0, st>>>(*g, parent, root, row_cnt);
+  k_row_tiles<<<(unsigned)utiles, kTile, 0, st>>>(row_cnt, units, tile64);
+  k_row_offsets<<<(unsigned)utiles, kTile, 0, st>>>(row_cnt, units, tile64, row_off, total);
   int64_t m_lcc = 0;
   FJ_CUDA(cudaMemcpyAsync(&m_lcc, total, 8, cudaMemcpyDeviceToHost, st));
   FJ_CUDA(cudaStreamSynchronize(st));
@@ -364,8 +378,8 @@ fj_status fj_lcc_device(const fj_graph* g, cudaStream_t st, fj_graph** out) {
     return fail(FJ_ERR_OOM);
   }
   count_launches(1);
-  k_lcc_write<<<grid_of(std::max<int64_t>(g->n_long * 32, n), 256), 256, 0, st>>>(*g, parent, root, row_off,
-                                                                                  new_id, src, dst, w);
+  k_lcc_write<<<grid_of(std::max<int64_t>(g->n_chunks * 32, n), 256), 256, 0, st>>>(*g, parent, root, row_off,
+                                                                                    new_id, src, dst, w);
   if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
   // ---- 4. build it like an upload (the pairs are distinct unless g merged
   // repeated pairs, whose parallel entries are kept as such)
