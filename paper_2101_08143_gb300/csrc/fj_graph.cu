@@ -794,10 +794,20 @@ void fj_free_graph_arrays(fj_graph* g, cudaStream_t st) {
 }
 
 // Called by the C ABI (fj_api.cpp).  src/dst/w are device pointers.
-fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m,
-                                const int32_t* src, const int32_t* dst, const float* w,
-                                bool merge_duplicates, fj_graph** out, int32_t* copy_src,
-                                int32_t* copy_dst, float* copy_w) {
+// Host words of a build: [0] n_long [1] n_nz [2] n_slices [3] nnz
+// [4] n_chunks [5] sliced-ELL entries [6] error bits [7] first invalid edge
+// [8] first repeated pair.
+constexpr int kBuildWords = 9;
+
+// First half of a build: every kernel and, last, the copy of the sizes and
+// the validation words (kBuildWords int64) to host_words, all enqueued on st.
+// *pending receives the graph, whose sizes fj_build_graph_end fills in once
+// that copy has completed; host_words must stay valid until then (page-locked
+// memory for an asynchronous copy).
+fj_status fj_build_graph_begin(int device, cudaStream_t st, int64_t n, int64_t m, const int32_t* src,
+                               const int32_t* dst, const float* w, bool merge_duplicates, int64_t* host_words,
+                               fj_graph** pending, int32_t* copy_src, int32_t* copy_dst, float* copy_w) {
+  fj_graph** out = pending;
   const int64_t N = 2 * m;
   const bool weighted = (w != nullptr);
   Pool pool(st);
@@ -807,7 +817,7 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   };
   // dcnt: [0] n_long [1] n_nz [2] n_slices [3] nnz [4] n_chunks [5] sliced-ELL
   // entries [6] error bits [7] first invalid edge [8] first repeated pair
-  int64_t* dcnt = pool.get<int64_t>(9);
+  int64_t* dcnt = pool.get<int64_t>(kBuildWords);
   int32_t* deg = pool.get<int32_t>(n);
   if (pool.failed) return oom();
   FJ_CUDA(cudaMemsetAsync(dcnt, 0, 56, st));
@@ -967,11 +977,24 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
     if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
   }
 
-  // ---- sizes and the validation result back to the host (one round trip)
-  int64_t hc[9];
-  if (cudaMemcpyAsync(hc, dcnt, sizeof(hc), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
+  // ---- sizes and the validation result to the host (the build's one round
+  // trip, completed by fj_build_graph_end)
+  if (cudaMemcpyAsync(host_words, dcnt, kBuildWords * sizeof(int64_t), cudaMemcpyDeviceToHost, st) !=
+      cudaSuccess)
     return fail(FJ_ERR_CUDA);
+  *out = g;
+  return FJ_OK;
+}
+
+// Second half: checks the validation words and fills in the sizes, or frees
+// the graph (stream-ordered on st) and reports the bad input.
+fj_status fj_build_graph_end(fj_graph* g, const int64_t* hc, cudaStream_t st, fj_graph** out) {
+  *out = nullptr;
+  auto fail = [&](fj_status code) {
+    fj_free_graph_arrays(g, st);
+    delete g;
+    return code;
+  };
   if (hc[6] & (kErrBadId | kErrBadWeight)) {
     set_error("fj_graph_upload: edge %llu has %s", (unsigned long long)hc[7],
               (hc[6] & kErrBadId) ? "a node id outside [0, n)" : "a weight that is not finite and > 0");
@@ -993,6 +1016,25 @@ fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t 
   g->n_units = g->n_chunks + g->n_slices;
   *out = g;
   return FJ_OK;
+}
+
+// Both halves with the host waiting in between.
+fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m, const int32_t* src,
+                                const int32_t* dst, const float* w, bool merge_duplicates, fj_graph** out,
+                                int32_t* copy_src, int32_t* copy_dst, float* copy_w) {
+  int64_t hc[kBuildWords];
+  fj_graph* g = nullptr;
+  *out = nullptr;
+  fj_status rc = fj_build_graph_begin(device, st, n, m, src, dst, w, merge_duplicates, hc, &g, copy_src, copy_dst,
+                                      copy_w);
+  if (rc != FJ_OK) return rc;
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    fj_free_graph_arrays(g, st);
+    delete g;
+    return cuda_fail(e, "fj_graph_upload");
+  }
+  return fj_build_graph_end(g, hc, st, out);
 }
 
 fj_status fj_free_graph_device(fj_graph* g, cudaStream_t st) {

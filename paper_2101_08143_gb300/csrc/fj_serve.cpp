@@ -28,9 +28,11 @@
 
 #include "fj_internal.cuh"
 
-fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m, const int32_t* src,
-                                const int32_t* dst, const float* w, bool merge_duplicates, fj_graph** out, int32_t* copy_src = nullptr, int32_t* copy_dst = nullptr,
-                                float* copy_w = nullptr);
+fj_status fj_build_graph_begin(int device, cudaStream_t st, int64_t n, int64_t m, const int32_t* src,
+                               const int32_t* dst, const float* w, bool merge_duplicates, int64_t* host_words,
+                               fj_graph** pending, int32_t* copy_src = nullptr, int32_t* copy_dst = nullptr,
+                               float* copy_w = nullptr);
+fj_status fj_build_graph_end(fj_graph* g, const int64_t* host_words, cudaStream_t st, fj_graph** out);
 void fj_free_graph_arrays(fj_graph* g, cudaStream_t st);
 size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms);
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k, const double* s, double* z,
@@ -40,6 +42,11 @@ fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32
 namespace fj {
 
 constexpr int kSlotMaxK = 1024;  // columns per request (pinned result buffers)
+constexpr int kBuildWords = 9;   // a graph build's host words (sizes, validation)
+// page-locked bytes per slot: quant [k][5] | resid [k] | status words, then
+// the build words
+constexpr size_t kSlotResultBytes = (size_t)kSlotMaxK * 6 * 8 + 64 * 12;
+constexpr size_t kSlotPinnedBytes = kSlotResultBytes + kBuildWords * 8;
 
 struct Request {
   uint64_t id = 0;
@@ -56,6 +63,7 @@ struct Request {
   // running state
   int slot = -1;
   fj_graph* own_graph = nullptr;
+  fj_graph* building = nullptr;  // inline graph whose build is in flight (ev marks its end)
   char* dev = nullptr;  // one device allocation: s | quant | resid | status | workspace
   cudaEvent_t ev = nullptr;
   int launches = 0;
@@ -127,43 +135,67 @@ void finish(Server& S, Request* r, fj_status rc) {
   r->info.columns = r->k;
 }
 
-// Launches the whole request on its slot's stream.  Returns an error code if
-// it could not be started (the request then completes with that code).
-fj_status start(Server& S, Request* r) {
+int64_t* build_words(Server& S, const Request* r) {
+  return reinterpret_cast<int64_t*>(reinterpret_cast<char*>(S.slots[r->slot].pinned) + kSlotResultBytes);
+}
+
+// Launches the request's own graph build on its slot's stream and records
+// r->ev after the copy of the build's host words; the solve starts once that
+// event has completed (start_solve), so the worker thread never waits for a
+// build.  Returns an error code if it could not be started.
+fj_status start_build(Server& S, Request* r) {
   Slot& sl = S.slots[r->slot];
   cudaStream_t st = sl.stream;
   cudaSetDevice(S.device);
-  const fj_graph* g = r->graph;
-  if (!g) {
-    int32_t *ds = nullptr, *dd = nullptr;
-    float* dw = nullptr;
-    const size_t eb = (size_t)std::max<int64_t>(r->m, 1) * 4;
-    if (malloc_async(&ds, eb, st) != cudaSuccess || malloc_async(&dd, eb, st) != cudaSuccess ||
-        (r->weighted && malloc_async(&dw, eb, st) != cudaSuccess)) {
-      cudaGetLastError();
-      if (ds) cudaFreeAsync(ds, st);
-      if (dd) cudaFreeAsync(dd, st);
-      set_error("fj_submit_edges: out of device memory for the edge list");
-      return FJ_ERR_OOM;
-    }
-    if (r->m > 0) {
-      cudaMemcpyAsync(ds, r->src.data(), r->m * 4, cudaMemcpyHostToDevice, st);
-      cudaMemcpyAsync(dd, r->dst.data(), r->m * 4, cudaMemcpyHostToDevice, st);
-      if (r->weighted) cudaMemcpyAsync(dw, r->w.data(), r->m * 4, cudaMemcpyHostToDevice, st);
-    }
+  int32_t *ds = nullptr, *dd = nullptr;
+  float* dw = nullptr;
+  const size_t eb = (size_t)std::max<int64_t>(r->m, 1) * 4;
+  if (malloc_async(&ds, eb, st) != cudaSuccess || malloc_async(&dd, eb, st) != cudaSuccess ||
+      (r->weighted && malloc_async(&dw, eb, st) != cudaSuccess)) {
+    cudaGetLastError();
+    if (ds) cudaFreeAsync(ds, st);
+    if (dd) cudaFreeAsync(dd, st);
+    set_error("fj_submit_edges: out of device memory for the edge list");
+    return FJ_ERR_OOM;
+  }
+  if (r->m > 0) {
+    cudaMemcpyAsync(ds, r->src.data(), r->m * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dd, r->dst.data(), r->m * 4, cudaMemcpyHostToDevice, st);
+    if (r->weighted) cudaMemcpyAsync(dw, r->w.data(), r->m * 4, cudaMemcpyHostToDevice, st);
+  }
+  fj_graph* pending = nullptr;
+  fj_status rc = fj_build_graph_begin(S.device, st, r->n, r->m, ds, dd, r->weighted ? dw : nullptr,
+                                      (r->opts.flags & FJ_MERGE_DUPLICATES) != 0, build_words(S, r), &pending);
+  cudaFreeAsync(ds, st);
+  cudaFreeAsync(dd, st);
+  if (dw) cudaFreeAsync(dw, st);
+  if (rc != FJ_OK) return rc;
+  r->building = pending;
+  cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
+  cudaEventRecord(r->ev, st);
+  return FJ_OK;
+}
+
+// Launches the solve on the slot's stream (the graph is resident: the
+// caller's, or the request's own once its build has ended).
+fj_status start_solve(Server& S, Request* r) {
+  Slot& sl = S.slots[r->slot];
+  cudaStream_t st = sl.stream;
+  cudaSetDevice(S.device);
+  if (r->building) {
     fj_graph* og = nullptr;
-    fj_status rc = fj_build_graph_device(S.device, st, r->n, r->m, ds, dd, r->weighted ? dw : nullptr,
-                                         (r->opts.flags & FJ_MERGE_DUPLICATES) != 0, &og);
-    cudaFreeAsync(ds, st);
-    cudaFreeAsync(dd, st);
-    if (dw) cudaFreeAsync(dw, st);
+    fj_graph* g0 = r->building;
+    r->building = nullptr;
+    cudaEventDestroy(r->ev);
+    r->ev = nullptr;
+    fj_status rc = fj_build_graph_end(g0, build_words(S, r), st, &og);
     if (rc != FJ_OK) return rc;
     r->own_graph = og;
-    g = og;
     std::vector<int32_t>().swap(r->src);
     std::vector<int32_t>().swap(r->dst);
     std::vector<float>().swap(r->w);
   }
+  const fj_graph* g = r->graph ? r->graph : r->own_graph;
   const int64_t n = g->n;
   int Ks[64], launches = 0;
   for (int col = 0; col < r->k;) {
@@ -239,6 +271,29 @@ void collect(Server& S, Request* r) {
   finish(S, r, rc);
 }
 
+// A request that could not be started (or whose graph was bad): free what
+// it holds on its slot's stream, release the slot, complete it with rc.
+void abandon(Server& S, Request* r, fj_status rc) {
+  cudaStream_t st = S.slots[r->slot].stream;
+  S.slots[r->slot].busy = false;
+  S.used -= (int64_t)r->mem_est;
+  if (r->own_graph) {
+    fj_free_graph_arrays(r->own_graph, st);
+    delete r->own_graph;
+    r->own_graph = nullptr;
+  }
+  if (r->dev) {
+    cudaFreeAsync(r->dev, st);
+    r->dev = nullptr;
+  }
+  if (r->ev) {
+    cudaEventDestroy(r->ev);
+    r->ev = nullptr;
+  }
+  finish(S, r, rc);
+  S.cv_done.notify_all();
+}
+
 void worker_loop(Server* Sp) {
   Server& S = *Sp;
   cudaSetDevice(S.device);
@@ -246,18 +301,30 @@ void worker_loop(Server* Sp) {
   while (true) {
     if (S.stop) break;
     bool progress = false;
-    // retire finished requests
+    // requests whose graph build ended start their solve; finished requests
+    // retire (only this thread changes the in-flight list)
     for (size_t i = 0; i < S.inflight.size();) {
       Request* r = S.inflight[i];
-      if (cudaEventQuery(r->ev) == cudaSuccess) {
+      if (cudaEventQuery(r->ev) != cudaSuccess) {
+        ++i;
+        continue;
+      }
+      progress = true;
+      if (r->building) {
+        lock.unlock();
+        const fj_status rc = start_solve(S, r);
+        lock.lock();
+        if (rc == FJ_OK) {
+          ++i;
+          continue;
+        }
+        abandon(S, r, rc);
+      } else {
         collect(S, r);
         S.slots[r->slot].busy = false;
         S.used -= (int64_t)r->mem_est;
-        S.inflight.erase(S.inflight.begin() + i);
-        progress = true;
-      } else {
-        ++i;
       }
+      S.inflight.erase(S.inflight.begin() + i);
     }
     if (progress) S.cv_done.notify_all();
     // admit in arrival order while a slot and the memory budget allow
@@ -272,22 +339,12 @@ void worker_loop(Server* Sp) {
       S.used += (int64_t)r->mem_est;
       r->t_start = std::chrono::steady_clock::now();
       lock.unlock();
-      fj_status rc = start(S, r);
+      const fj_status rc = r->graph ? start_solve(S, r) : start_build(S, r);
       lock.lock();
-      if (rc != FJ_OK) {
-        S.slots[slot].busy = false;
-        S.used -= (int64_t)r->mem_est;
-        if (r->own_graph) {
-          fj_free_graph_arrays(r->own_graph, S.slots[slot].stream);
-          delete r->own_graph;
-          r->own_graph = nullptr;
-        }
-        if (r->dev) cudaFreeAsync(r->dev, S.slots[slot].stream);
-        finish(S, r, rc);
-        S.cv_done.notify_all();
-      } else {
+      if (rc != FJ_OK)
+        abandon(S, r, rc);
+      else
         S.inflight.push_back(r);
-      }
       progress = true;
     }
     if (!progress) {
@@ -300,6 +357,19 @@ void worker_loop(Server* Sp) {
   // shutdown: drain what is on the GPU, drop what is queued
   for (Request* r : S.inflight) {
     cudaStreamSynchronize(S.slots[r->slot].stream);
+    if (r->building) {  // a build that ended: drop its graph
+      fj_graph* og = nullptr;
+      if (fj_build_graph_end(r->building, build_words(S, r), S.slots[r->slot].stream, &og) == FJ_OK) {
+        fj_free_graph_arrays(og, S.slots[r->slot].stream);
+        delete og;
+      }
+      r->building = nullptr;
+      cudaEventDestroy(r->ev);
+      r->ev = nullptr;
+      cudaStreamSynchronize(S.slots[r->slot].stream);
+      finish(S, r, FJ_ERR_ARG);
+      continue;
+    }
     collect(S, r);
   }
   S.inflight.clear();
@@ -321,7 +391,7 @@ Server* server_create(int device, int num_sms) {
   S->slots.resize(S->max_inflight);
   for (auto& sl : S->slots) {
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMallocHost(&sl.pinned, (size_t)kSlotMaxK * 6 * 8 + 64 * 12) != cudaSuccess) {
+        cudaMallocHost(&sl.pinned, kSlotPinnedBytes) != cudaSuccess) {
       cudaGetLastError();
       delete S;
       return nullptr;
@@ -342,7 +412,7 @@ fj_status server_config(Server* S, int32_t max_inflight, int64_t budget, int32_t
       S->slots.resize(max_inflight);
       for (size_t i = old; i < S->slots.size(); ++i) {
         if (cudaStreamCreateWithFlags(&S->slots[i].stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaMallocHost(&S->slots[i].pinned, (size_t)kSlotMaxK * 6 * 8 + 64 * 12) != cudaSuccess) {
+            cudaMallocHost(&S->slots[i].pinned, kSlotPinnedBytes) != cudaSuccess) {
           cudaGetLastError();
           S->slots.resize(i);
           set_error("fj_serve_config: could not create slot %zu", i);
