@@ -259,7 +259,9 @@ def serving_run(ctx, fj, n_requests=240, seed=4, rate_frac=0.5):
     weights U(0,1], 1-16 opinion vectors) through fj_submit_edges / fj_poll.
     First the saturation throughput (all requests at once), then an open
     loop at rate_frac of it; latency = submit to completion.  The generated
-    graphs are simple, so requests pass FJ_MERGE_DUPLICATES."""
+    graphs are simple, so requests pass FJ_MERGE_DUPLICATES.  All requests
+    are prepared before the clock starts; submitting one still copies its
+    edge list and opinions (the API copies inputs at the call)."""
     import threading
     rng = np.random.default_rng(seed)
     pool = []
@@ -275,7 +277,9 @@ def serving_run(ctx, fj, n_requests=240, seed=4, rate_frac=0.5):
     for r in range(n_requests):
         gg = pool[int(rng.integers(0, len(pool)))]
         k = int(rng.integers(1, 17))
-        reqs.append((gg, rng.random((gg.n, k))))
+        # s in the API's layout (n x k column-major), so that submitting
+        # copies it once and converts nothing
+        reqs.append((gg, rng.random((k, gg.n)).T))
 
     def run(gaps):
         t_sub, t_done = [0.0] * len(reqs), [0.0] * len(reqs)

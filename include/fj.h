@@ -241,10 +241,12 @@ fj_status fj_quantities(fj_ctx* ctx, const fj_graph* g, int32_t k,
  */
 
 /* Sets the serving limits: at most max_inflight requests on the GPU at once
- * (default 8; 0 keeps the current value), a device-memory budget for admitted
- * requests (default half the free memory when serving starts; <= 0 keeps the
- * current value) and a cap on the thread blocks of each request's solve
- * (0: sized by the request alone; < 0 keeps the current value).
+ * (default 16; 0 keeps the current value), a device-memory budget for
+ * admitted requests (default half the free memory when serving starts; <= 0
+ * keeps the current value) and a cap on the thread blocks of each request's
+ * solve (0, the default: the device's co-resident solve blocks divided by
+ * max_inflight, so that the in-flight requests run side by side; < 0 keeps
+ * the current value).
  * Errors: FJ_ERR_ARG, FJ_ERR_CUDA. */
 fj_status fj_serve_config(fj_ctx* ctx, int32_t max_inflight,
                           int64_t mem_budget_bytes,

@@ -62,6 +62,7 @@ struct Request {
   size_t mem_est = 0;
   // running state
   int slot = -1;
+  int block_cap = 0;  // grid cap of the request's solve, fixed at admission
   fj_graph* own_graph = nullptr;
   fj_graph* building = nullptr;  // inline graph whose build is in flight (ev marks its end)
   char* dev = nullptr;  // one device allocation: s | quant | resid | status | workspace
@@ -84,9 +85,9 @@ struct Slot {
 struct Server {
   int device = 0;
   int num_sms = 0;
-  int max_inflight = 8;
+  int max_inflight = 16;
   int64_t budget = 0;
-  int max_blocks = 0;  // per-request grid cap (0: size-based only)
+  int max_blocks = 0;  // per-request grid cap (0: automatic, see block_cap)
   int64_t used = 0;
   uint64_t next_id = 1;
   bool stop = false;
@@ -95,7 +96,7 @@ struct Server {
   std::deque<Request*> pending;
   std::vector<Request*> inflight;
   std::unordered_map<uint64_t, Request*> all;
-  std::vector<Slot> slots;
+  std::deque<Slot> slots;  // grows in place: references to slots stay valid
   std::thread worker;
   std::string init_error;
 
@@ -126,6 +127,14 @@ size_t estimate_bytes(const Request& r, int num_sms) {
   const int inner = r.opts.precision == FJ_PREC_FP64 ? 8 : 4;
   b += (size_t)n * K * (24 + 6 * inner) + (size_t)num_sms * 4 * 16 * K * 16 + (size_t)n * r.k * 8 + (1 << 20);
   return b;
+}
+
+// Grid cap of one request's solve: the configured one, else the device's
+// co-resident solve blocks (two per SM) shared by the in-flight requests, so
+// that they run side by side instead of one at a time.
+int block_cap(const Server& S) {
+  if (S.max_blocks > 0) return S.max_blocks;
+  return std::max(1, 2 * S.num_sms / std::max(1, S.max_inflight));
 }
 
 void finish(Server& S, Request* r, fj_status rc) {
@@ -223,7 +232,7 @@ fj_status start_solve(Server& S, Request* r) {
   fj_opts o = r->opts;
   o.flags = FJ_DEVICE_PTRS;
   fj_status rc = fj_solve_device(g, st, S.num_sms, r->k, ds, nullptr, dq, dres, dstat, r->dev + s_bytes + small,
-                                 ws, o, &r->launches, S.max_blocks, nullptr);
+                                 ws, o, &r->launches, r->block_cap, nullptr);
   if (rc != FJ_OK) return rc;
   cudaMemcpyAsync(sl.pinned, dq, (size_t)r->k * 6 * 8 + (size_t)launches * 12, cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(r->dev, st);
@@ -336,6 +345,7 @@ void worker_loop(Server* Sp) {
       while (S.slots[slot].busy) ++slot;
       S.slots[slot].busy = true;
       r->slot = slot;
+      r->block_cap = block_cap(S);
       S.used += (int64_t)r->mem_est;
       r->t_start = std::chrono::steady_clock::now();
       lock.unlock();
