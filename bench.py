@@ -94,7 +94,10 @@ def _workload_desc(spec, g, nnz=None):
 
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 50 ms; stop() keeps those taken between
+    mark_start() and mark_end() (the timed region), or all of them when none
+    fall inside."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -102,16 +105,23 @@ class ClockSampler:
         self.proc = None
         self.path = None
         self.device = device_index
+        self.t0 = self.t1 = None
         try:
             import tempfile
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
@@ -121,26 +131,32 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
+        import datetime
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
                 p = [x.strip() for x in line.split(",")]
-                if len(p) < 9:
+                if len(p) < 10:
                     continue
                 try:
-                    sm.append(float(p[1]))
-                    mx.append(float(p[2]))
+                    ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(p[2]), float(p[3]), p[6:10]))
                 except ValueError:
                     continue
-                for nm, v in zip(names, p[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(nm)
         os.unlink(self.path)
-        if not sm:
+        inside = [r for r in rows if self.t0 is not None and self.t1 is not None and self.t0 <= r[0] <= self.t1]
+        window = "timed region" if inside else "whole run"
+        use = inside or rows
+        if not use:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        reasons = set()
+        for r in use:
+            for nm, v in zip(names, r[3]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median([r[1] for r in use])), "sm_max_mhz": float(max(r[2] for r in use)),
+                "reasons": sorted(reasons), "samples": len(use), "window": window}
 
 
 def _bytes_per_launch(n, nnz, weighted, k, iters, refines):
@@ -423,6 +439,7 @@ def main():
         gr.free()
         return q, info
 
+    clocks = ClockSampler(local)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             q, info = step()
@@ -435,7 +452,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
+    clocks.mark_start()
     launches0 = lib.fj_kernel_launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
@@ -449,6 +466,7 @@ def main():
             evs[i][1].record(stream)
             infos.append(info)
     torch.cuda.synchronize()
+    clocks.mark_end()
     wall = time.perf_counter() - wall0
     launches = lib.fj_kernel_launches() - launches0
     clk = clocks.stop()
