@@ -80,10 +80,15 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _workload_desc(spec, g, nnz=None):
-    d = {"workload": (f"chung-lu n={spec['n']:,} m={spec['m']:,} exponent={spec['exponent']} "
-                      f"w~U(0,1] f32, k={spec['k']} s~U[0,1], mixed PCG to rel. residual {TOL:g}"),
-         "n": g.n, "m": g.m, "k": spec["k"], "tol": TOL,
+def _workload_desc(spec, g, k, nnz=None):
+    kind = "chung-lu" if spec["kind"] == "cl" else "erdos-renyi"
+    shape = f"exponent={spec['exponent']} " if spec["kind"] == "cl" else ""
+    weights = "w~U(0,1] f32" if spec.get("weighted") else "unit w"
+    opinions = {"uniform": "s~U[0,1]", "mix": "s half U[0,1], half Beta(1/2,1/2)"}.get(
+        spec.get("opinions", "uniform"), spec.get("opinions"))
+    d = {"workload": (f"{kind} n={spec['n']:,} m={spec['m']:,} {shape}{weights}, k={k} {opinions}, "
+                      f"mixed PCG to rel. residual {TOL:g}"),
+         "n": g.n, "m": g.m, "k": k, "tol": TOL,
          "step": "graph ingest + centring + solve + 5 quantities + z (inputs resident in HBM)",
          "upload_flags": "FJ_MERGE_DUPLICATES (the generated graph is simple; the default strict "
                          "check for repeated pairs is skipped)",
@@ -91,6 +96,18 @@ def _workload_desc(spec, g, nnz=None):
     if nnz is not None:
         d["nnz"] = nnz
     return d
+
+
+def _launch_widths(k):
+    """Columns per solve launch: 32 at a time, the remainder in 16/8/4/2/1."""
+    out = []
+    while k > 0:
+        w = 32
+        while w > k:
+            w //= 2
+        out.append(w)
+        k -= w
+    return out
 
 
 class ClockSampler:
@@ -141,11 +158,15 @@ class ClockSampler:
                     continue
                 try:
                     ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    ts = None
+                try:
                     rows.append((ts, float(p[2]), float(p[3]), p[6:10]))
                 except ValueError:
                     continue
         os.unlink(self.path)
-        inside = [r for r in rows if self.t0 is not None and self.t1 is not None and self.t0 <= r[0] <= self.t1]
+        inside = [r for r in rows if r[0] is not None and self.t0 is not None and self.t1 is not None
+                  and self.t0 <= r[0] <= self.t1]
         window = "timed region" if inside else "whole run"
         use = inside or rows
         if not use:
@@ -370,7 +391,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _workload_desc(spec, g),
+            "config": _workload_desc(spec, g, 1),
             "latency_ms": {"p50": 1000 * float(np.percentile(times, 50)),
                            "p99": 1000 * float(np.percentile(times, 99))},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
@@ -391,6 +412,8 @@ def main():
     ap.add_argument("--cpu-solves", type=int, default=3, help="oracle solves in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--k", type=int, default=None,
+                    help="opinion vectors per step (default: the workload's own)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -415,9 +438,13 @@ def main():
 
     lib = fj.load()
     spec = synth.WORKLOADS[args.workload]
+    # the side measurements (precision modes, warm start, LCC, serving, CPU
+    # oracle) run on the default workload only; the larger workloads time
+    # the step alone
+    full = args.workload == WORKLOAD and args.k is None
     g = synth.make_graph(spec)
-    k = spec["k"]
-    s_host = synth.make_opinions(spec, g.n)  # n x k, column-major
+    k = spec["k"] if args.k is None else args.k
+    s_host = synth.make_opinions(spec, g.n, k)  # n x k, column-major
     weighted = g.w is not None
 
     ctx = fj.Context(local)
@@ -477,8 +504,12 @@ def main():
     kern_ms = float(np.mean([i["device_ms"] for i in infos]))
     iters = int(np.mean([i["iterations"] for i in infos]))
     refines = int(np.mean([i["refinements"] for i in infos]))
-    algo = _bytes_per_launch(g.n, nnz, weighted, k, iters, refines)
+    # iterations are the maximum over launches (k > 32), so for several
+    # launches the byte count is an upper bound
+    algo = sum(_bytes_per_launch(g.n, nnz, weighted, K, iters, refines) for K in _launch_widths(k))
     achieved = algo / (kern_ms / 1000.0) / 1e9
+    widths = _launch_widths(k)
+    kernel_name = f"k_solve<float,{widths[0]}>" + (f" x {len(widths)} launches" if len(widths) > 1 else "")
     peak, peak_kind = _peaks()
 
     # solve-only rate on a resident graph (same opts), for context
@@ -518,10 +549,10 @@ def main():
     h2d = g.m * 4 * (3 if weighted else 2) + g.n * k * 8
     d2h = g.n * k * 8 + k * 5 * 8
 
-    compare = precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush)
-    warm = warm_start_run(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush)
-    lcc = lcc_run(ctx, torch, g, src_d, dst_d, w_d, stream)
-    serving = serving_run(ctx, fj) if not args.no_serving else None
+    compare = precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush) if full else None
+    warm = warm_start_run(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush) if full else None
+    lcc = lcc_run(ctx, torch, g, src_d, dst_d, w_d, stream) if full else None
+    serving = serving_run(ctx, fj) if full and not args.no_serving else None
 
     line = None
     if rank == 0:
@@ -530,7 +561,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
-            "config": _workload_desc(spec, g, nnz),
+            "config": _workload_desc(spec, g, k, nnz),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                            "p99": float(np.percentile(step_ms, 99))},
             "solve_only": {"value": 1000.0 / float(np.mean(solve_ms)), "unit": "solves/s",
@@ -543,11 +574,11 @@ def main():
             # per second of the whole step
             "edge_iterations_per_s": {"kernel": nnz * k * iters / (kern_ms / 1000.0),
                                       "step": nnz * k * iters * value / k},
-            "roofline": {"kernel": "k_solve<float,1>", "bound": "hbm", "achieved": achieved,
+            "roofline": {"kernel": kernel_name, "bound": "hbm", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": f"{peak_kind} (hbm_gbs, burst copy)",
-                         "traffic": _profiled_traffic(), "algorithmic_bytes": algo,
-                         "kernel_ms": kern_ms},
+                         "traffic": _profiled_traffic() if full else None,
+                         "algorithmic_bytes": algo, "kernel_ms": kern_ms},
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "p50_ms": float(np.percentile(e2e_ms, 50))},
             "gpu_launches": int(launches),
@@ -561,7 +592,7 @@ def main():
             "serving": serving,
         }
     ctx.close()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and full and not args.no_cpu_baseline:
         s0 = s_host[:, 0]
         v, dt = run_cpu_baseline(g, s0, args.cpu_solves)
         line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
