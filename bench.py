@@ -290,6 +290,56 @@ def lcc_run(ctx, torch, g, src_d, dst_d, w_d, stream, reps=3):
     return out
 
 
+def small_graph_run(ctx, fj, torch, stream, reps=200):
+    """The Erdos-Renyi workload n = 2,000, m = 10,000, unit weights, one
+    s ~ U[0,1], solved to relative residual 1e-10: latency of the plain
+    float64 solve + quantities and of the mixed one, with the default grid
+    and with the grid fj_tune picks for this graph (tune_kernel_ms: its
+    timings by grid, "0" being the default sizing).  Graph and s stay
+    resident; the whole problem fits in L2, so no flush.  Wall time is the
+    API call as the caller sees it (it returns after the results are back)."""
+    spec = synth.WORKLOADS["er_n2k_d10"]
+    g = synth.make_graph(spec)
+    s = synth.make_opinions(spec, g.n)[:, 0]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    src_d = torch.from_numpy(g.src).to(dev)
+    dst_d = torch.from_numpy(g.dst).to(dev)
+    s_d = torch.from_numpy(s).to(dev)
+    z_d = torch.empty_like(s_d)
+    out = {"workload": "erdos-renyi n=2,000 m=10,000 unit w, k=1 s~U[0,1], rel. residual 1e-10"}
+
+    def timed(opts):
+        wall, dev_ms = [], []
+        for i in range(reps + 5):
+            t0 = time.perf_counter()
+            _, _, info = ctx.solve(gr, s_d, opts=opts, z_out=z_d)
+            if i >= 5:
+                wall.append(1e6 * (time.perf_counter() - t0))
+                dev_ms.append(info["device_ms"])
+        return wall, dev_ms, info
+
+    with torch.cuda.stream(stream):
+        gr = ctx.upload(g.n, src_d, dst_d, None)
+        for name, prec in (("fp64", fj.PREC_FP64), ("mixed", fj.PREC_MIXED)):
+            opts = fj.default_opts(tol=1e-10, precision=prec)
+            wall0, dev0, info = timed(opts)
+            tune = ctx.tune(gr, s_d, opts=opts, repeats=10)
+            wall1, dev1, info1 = timed(opts)
+            out[name] = {"iterations": info["iterations"], "refinements": info["refinements"],
+                         "default_grid": {"blocks": info["blocks"],
+                                          "us_p50": float(np.percentile(wall0, 50)),
+                                          "us_p99": float(np.percentile(wall0, 99)),
+                                          "kernel_us_p50": 1e3 * float(np.percentile(dev0, 50))},
+                         "tuned_grid": {"blocks": info1["blocks"],
+                                        "us_p50": float(np.percentile(wall1, 50)),
+                                        "us_p99": float(np.percentile(wall1, 99)),
+                                        "kernel_us_p50": 1e3 * float(np.percentile(dev1, 50))},
+                         "solves_per_s": 1e6 / float(np.mean(wall1)),
+                         "tune_kernel_ms": {str(b): ms for b, ms in tune["grids"]}}
+        gr.free()
+    return out
+
+
 def serving_run(ctx, fj, n_requests=240, seed=4, rate_frac=0.5):
     """A Poisson stream of requests that bring their own graph (Erdos-Renyi or
     Chung-Lu, n log-uniform in [10^3, 10^5], average degree U[4, 20],
@@ -552,6 +602,7 @@ def main():
     compare = precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush) if full else None
     warm = warm_start_run(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush) if full else None
     lcc = lcc_run(ctx, torch, g, src_d, dst_d, w_d, stream) if full else None
+    small = small_graph_run(ctx, fj, torch, stream) if full else None
     serving = serving_run(ctx, fj) if full and not args.no_serving else None
 
     line = None
@@ -589,6 +640,7 @@ def main():
             "precision_compare": compare,
             "warm_start": warm,
             "lcc": lcc,
+            "small_graph": small,
             "serving": serving,
         }
     ctx.close()

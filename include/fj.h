@@ -107,6 +107,7 @@ typedef struct fj_info {
   double device_ms;    /* device time of the solve kernels                   */
   int32_t status;      /* same as the return value of the call               */
   int32_t columns;     /* k                                                  */
+  int32_t blocks;      /* thread blocks of the solve's grid (largest launch)  */
 } fj_info;
 
 /* The five quantities of one opinion vector (Sec. 3.2 definitions). */
@@ -150,6 +151,13 @@ fj_status fj_set_stream(fj_ctx* ctx, void* stream);
  * several contexts run solves side by side on one GPU.
  * Errors: FJ_ERR_ARG (NULL ctx or negative cap). */
 fj_status fj_set_max_blocks(fj_ctx* ctx, int32_t max_blocks);
+
+/* Runs later solves of this context on a grid of exactly `blocks` thread
+ * blocks (at most the co-resident count, and at most the fj_set_max_blocks
+ * cap if one is set) instead of sizing it by the work; 0, the default,
+ * restores the sizing (or fj_tune's choice).  fj_info.blocks reports the
+ * grid a solve ran on.  Errors: FJ_ERR_ARG (NULL ctx or negative count). */
+fj_status fj_set_grid(fj_ctx* ctx, int32_t blocks);
 
 /* Builds the device CSR of I + L for an undirected weighted graph given as an
  * edge list (Sec. 2.1: A, d_i = sum_j w_ij, L = D - A).
@@ -229,6 +237,37 @@ fj_status fj_solve(fj_ctx* ctx, const fj_graph* g, int32_t k, const double* s,
 fj_status fj_quantities(fj_ctx* ctx, const fj_graph* g, int32_t k,
                         const double* s, fj_quant* out, const fj_opts* opts,
                         fj_info* info);
+
+/* Grid autotuner.  A solve is one persistent launch per group of at most
+ * 32 columns, so the launch shape left to choose per graph is its grid.  The
+ * default sizing takes about 16 CSR entries or nodes per thread, up to every
+ * co-resident block.  That suits large graphs; on small ones more blocks
+ * can win (more loads in flight, more float64 units), or fewer (each of the
+ * iteration's grid barriers costs more with more blocks).  fj_tune times
+ * solves of the k columns of s (solve kernels only, median of `repeats`
+ * after one warm-up) with the default sizing and with grids of exactly
+ * 2*SMs, SMs, SMs/2, ..., 1 blocks, keeps the fastest, and runs later
+ * fj_solve_ex / fj_solve_warm / fj_solve / fj_quantities calls on g with the
+ * same k and the same precision class (float64 or not) on it, unless the
+ * context's fj_set_grid asks for another grid; the fj_set_max_blocks cap
+ * still applies.  A later fj_tune on g replaces the choice; fj_graph_free
+ * forgets it.  The grid changes only the order of the floating-point sums,
+ * so results stay within the solve's tolerance and are bit-reproducible for
+ * a fixed grid.
+ *   s        float64[n*k] opinions as for fj_solve_ex (host or device)
+ *   opts     solve options (NULL: defaults); FJ_TWO_SOLVES is rejected
+ *   repeats  timed solves per grid, 1 to 64
+ *   out      host output: the grids timed and their median device times
+ * Errors: FJ_ERR_ARG, and any error of the solves it runs. */
+#define FJ_TUNE_MAX 16
+typedef struct fj_tune_result {
+  int32_t best;                /* fastest grid in blocks; 0 = default     */
+  int32_t count;               /* grids timed                             */
+  int32_t blocks[FJ_TUNE_MAX]; /* the grids timed, 0 = default sizing     */
+  double ms[FJ_TUNE_MAX];      /* median device milliseconds of each      */
+} fj_tune_result;
+fj_status fj_tune(fj_ctx* ctx, const fj_graph* g, int32_t k, const double* s,
+                  const fj_opts* opts, int32_t repeats, fj_tune_result* out);
 
 /* ---------------------------------------------------------------------
  * Serving: continuous batching of solve requests (one worker thread per

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "fj_internal.cuh"
@@ -28,7 +29,7 @@ size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int n
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k,
                           const double* s, double* z, double* quant, double* resid, int* status,
                           char* ws, size_t ws_bytes, const fj_opts& o, int* launches_out,
-                          int max_blocks, const double* z0);
+                          int max_blocks, const double* z0, int* grid_out);
 
 namespace fj {
 struct Server;
@@ -121,6 +122,7 @@ struct fj_ctx {
   size_t z0_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int max_blocks = 0;  // 0: all co-resident blocks
+  int grid = 0;        // > 0: exactly this many blocks (fj_set_grid)
   std::mutex server_mu;
   fj::Server* server = nullptr;  // created by the first fj_submit / fj_serve_config
 };
@@ -153,6 +155,40 @@ const void* mapped_host(const void* p) {
     return nullptr;
   }
   return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
+// Grids chosen by fj_tune, per graph: (k, float64 or not) -> grid cap.
+struct TunedGrid {
+  int32_t k;
+  int32_t fp64;
+  int32_t blocks;
+};
+std::mutex g_tuned_mu;
+std::unordered_map<const fj_graph*, std::vector<TunedGrid>> g_tuned;
+
+int tuned_grid(const fj_graph* g, int32_t k, bool fp64) {
+  std::lock_guard<std::mutex> lock(g_tuned_mu);
+  auto it = g_tuned.find(g);
+  if (it == g_tuned.end()) return 0;
+  for (const TunedGrid& t : it->second)
+    if (t.k == k && t.fp64 == (int32_t)fp64) return t.blocks;
+  return 0;
+}
+
+void set_tuned_grid(const fj_graph* g, int32_t k, bool fp64, int32_t blocks) {
+  std::lock_guard<std::mutex> lock(g_tuned_mu);
+  std::vector<TunedGrid>& v = g_tuned[g];
+  for (TunedGrid& t : v)
+    if (t.k == k && t.fp64 == (int32_t)fp64) {
+      t.blocks = blocks;
+      return;
+    }
+  v.push_back({k, (int32_t)fp64, blocks});
+}
+
+void forget_tuned_grids(const fj_graph* g) {
+  std::lock_guard<std::mutex> lock(g_tuned_mu);
+  g_tuned.erase(g);
 }
 
 // Launch widths for k columns: 32 at a time, then 16, 8, 4, 2, 1.
@@ -269,6 +305,17 @@ fj_status fj_set_max_blocks(fj_ctx* c, int32_t max_blocks) {
   return FJ_OK;
 }
 
+// Runs later solves on exactly `blocks` blocks (0: size the grid by the
+// work, or by fj_tune's choice for the graph).
+fj_status fj_set_grid(fj_ctx* c, int32_t blocks) {
+  if (!c || blocks < 0) {
+    set_error("fj_set_grid: bad argument");
+    return FJ_ERR_ARG;
+  }
+  c->grid = blocks;
+  return FJ_OK;
+}
+
 fj_status fj_graph_upload(fj_ctx* c, int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
                           const float* w, uint32_t flags, fj_graph** out) {
   if (!c || !out) {
@@ -338,6 +385,7 @@ fj_status fj_graph_free(fj_ctx* c, fj_graph* g) {
     return FJ_ERR_ARG;
   }
   if (!g) return FJ_OK;
+  forget_tuned_grids(g);
   FJ_CUDA(cudaSetDevice(c->device));
   return fj_free_graph_device(g, c->stream);
 }
@@ -445,8 +493,14 @@ static fj_status solve_impl(fj_ctx* c, const fj_graph* g, int32_t k, const doubl
   FJ_CUDA(cudaMemsetAsync(dstat, 0, (size_t)launches * 3 * 4, c->stream));
   FJ_CUDA(cudaEventRecord(c->ev0, c->stream));
   int done_launches = 0;
+  // grid: the context's exact grid, else the one fj_tune chose for this
+  // graph and k, else sized by the work; the context's cap bounds all three
+  int grid = c->grid > 0 ? c->grid : tuned_grid(g, k, o.precision == FJ_PREC_FP64);
+  if (grid > 0 && c->max_blocks > 0) grid = std::min(grid, c->max_blocks);
+  const int grid_arg = grid > 0 ? -grid : c->max_blocks;
+  int grid_used = 0;
   rc = fj_solve_device(g, c->stream, c->num_sms, k, sd, zd, dq, dres, dstat, c->ws, c->ws_bytes, o,
-                       &done_launches, c->max_blocks, z0);
+                       &done_launches, grid_arg, z0, &grid_used);
   if (rc != FJ_OK) return rc;
   FJ_CUDA(cudaEventRecord(c->ev1, c->stream));
   std::vector<double> hq((size_t)cols * 5), hres(cols);
@@ -488,6 +542,7 @@ static fj_status solve_impl(fj_ctx* c, const fj_graph* g, int32_t k, const doubl
     info->device_ms = ms;
     info->status = rc;
     info->columns = k;
+    info->blocks = grid_used;
   }
   return rc;
 }
@@ -519,6 +574,61 @@ fj_status fj_quantities(fj_ctx* c, const fj_graph* g, int32_t k, const double* s
     return FJ_ERR_ARG;
   }
   return fj_solve_ex(c, g, k, s, nullptr, out, opts, info);
+}
+
+fj_status fj_tune(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, const fj_opts* opts,
+                  int32_t repeats, fj_tune_result* out) {
+  if (!c || !g || !s || !out || k < 1 || repeats < 1 || repeats > 64) {
+    set_error("fj_tune: ctx, graph, s and out must be non-NULL, k >= 1, 1 <= repeats <= 64");
+    return FJ_ERR_ARG;
+  }
+  memset(out, 0, sizeof(*out));
+  fj_opts o;
+  fj_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.flags & FJ_TWO_SOLVES) {
+    set_error("fj_tune: FJ_TWO_SOLVES is not tuned");
+    return FJ_ERR_ARG;
+  }
+  const bool fp64 = o.precision == FJ_PREC_FP64;
+  // candidates: the default sizing, then grids of 2*SMs, SMs, SMs/2, ..., 1
+  std::vector<int32_t> caps = {0};
+  for (int32_t b = 2 * c->num_sms; b >= 1; b /= 2) {
+    if ((int)caps.size() == FJ_TUNE_MAX) break;
+    caps.push_back(b);
+  }
+  const int saved_cap = c->max_blocks, saved_grid = c->grid;
+  c->max_blocks = 0;
+  // grid 0 must mean the default sizing here, not an earlier tuning
+  set_tuned_grid(g, k, fp64, 0);
+  int32_t best = 0;
+  double best_ms = 0.0;
+  fj_status rc = FJ_OK;
+  for (size_t i = 0; i < caps.size() && rc == FJ_OK; ++i) {
+    c->grid = caps[i];
+    std::vector<double> ms;
+    for (int r = 0; r <= repeats && rc == FJ_OK; ++r) {
+      fj_info info;
+      rc = solve_impl(c, g, k, s, nullptr, nullptr, nullptr, &o, &info);
+      if (r > 0) ms.push_back(info.device_ms);
+    }
+    if (rc != FJ_OK) break;
+    std::sort(ms.begin(), ms.end());
+    const double med = ms[ms.size() / 2];
+    out->blocks[i] = caps[i];
+    out->ms[i] = med;
+    out->count = (int32_t)i + 1;
+    if (i == 0 || med < best_ms) {
+      best = caps[i];
+      best_ms = med;
+    }
+  }
+  c->max_blocks = saved_cap;
+  c->grid = saved_grid;
+  if (rc != FJ_OK) return rc;
+  out->best = best;
+  set_tuned_grid(g, k, fp64, best);
+  return FJ_OK;
 }
 
 // ------------------------------------------------------------- serving

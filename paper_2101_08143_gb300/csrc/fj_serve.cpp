@@ -37,7 +37,7 @@ void fj_free_graph_arrays(fj_graph* g, cudaStream_t st);
 size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms);
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k, const double* s, double* z,
                           double* quant, double* resid, int* status, char* ws, size_t ws_bytes, const fj_opts& o,
-                          int* launches_out, int max_blocks, const double* z0);
+                          int* launches_out, int max_blocks, const double* z0, int* grid_out);
 
 namespace fj {
 
@@ -232,7 +232,7 @@ fj_status start_solve(Server& S, Request* r) {
   fj_opts o = r->opts;
   o.flags = FJ_DEVICE_PTRS;
   fj_status rc = fj_solve_device(g, st, S.num_sms, r->k, ds, nullptr, dq, dres, dstat, r->dev + s_bytes + small,
-                                 ws, o, &r->launches, r->block_cap, nullptr);
+                                 ws, o, &r->launches, r->block_cap, nullptr, &r->info.blocks);
   if (rc != FJ_OK) return rc;
   cudaMemcpyAsync(sl.pinned, dq, (size_t)r->k * 6 * 8 + (size_t)launches * 12, cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(r->dev, st);

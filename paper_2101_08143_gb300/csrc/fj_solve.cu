@@ -643,7 +643,7 @@ template <typename VI, int K>
 static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, const double* s,
                             int64_t ld, double* z, double* quant, double* resid, int* status,
                             char* ws, size_t ws_bytes, const fj_opts& o, int mode, int max_blocks,
-                            bool paper, const double* z0) {
+                            bool paper, const double* z0, int* grid_out) {
   auto kern = k_solve<VI, K>;
   const size_t red_bytes = (size_t)7 * kWarps * K * sizeof(double);
   const size_t stage = (K <= 4) ? 0 : (size_t)kWarps * kWideStageBytes;
@@ -673,13 +673,18 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   }
   const int64_t n = g->n;
   // grid: enough blocks for the work, at most what is co-resident
-  // about 16 path items per thread before the grid stops growing
+  // about 16 path items per thread before the grid stops growing; a
+  // negative max_blocks asks for exactly -max_blocks blocks instead
   const int64_t work = n * K + g->nnz * K;
   int64_t want = (work + kThreads * 16 - 1) / (kThreads * 16);
   if (want < 1) want = 1;
   int64_t cap = (int64_t)std::min(per_sm, kMaxBlocksPerSM) * num_sms;
-  if (max_blocks > 0 && cap > max_blocks) cap = max_blocks;
+  if (max_blocks < 0)
+    want = -(int64_t)max_blocks;
+  else if (max_blocks > 0 && cap > max_blocks)
+    cap = max_blocks;
   const int blocks = (int)std::min(want, cap);
+  if (grid_out && *grid_out < blocks) *grid_out = blocks;
 
   // carve the workspace
   const int64_t NK = n * K;
@@ -761,10 +766,13 @@ size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int n
 // Runs the solve for columns [0, k) of s (column-major, leading dim n, all
 // device pointers) in launches of K = 32, 16, ..., 1 columns.
 // quant: device [k][5]; resid: device [k]; status: device int[3 * launches].
+// max_blocks > 0 caps each launch's grid, < 0 asks for exactly -max_blocks
+// blocks (at most the co-resident count), 0 sizes it by the work.
+// *grid_out (if given) is raised to the largest grid launched.
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k,
                           const double* s, double* z, double* quant, double* resid, int* status,
                           char* ws, size_t ws_bytes, const fj_opts& o, int* launches_out,
-                          int max_blocks, const double* z0) {
+                          int max_blocks, const double* z0, int* grid_out) {
   int mode = o.precision == FJ_PREC_FP64 ? kModeFP64 : (o.precision == FJ_PREC_FP32 ? kModeFP32 : kModeMixed);
   // two-solve mode: 2k launch columns (s_j as is, s_j centred), quant and
   // resid per launch column; every launch starts at an even column
@@ -786,10 +794,10 @@ fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32
 #define FJ_LAUNCH(KK)                                                                                  \
   if (mode == kModeFP64)                                                                               \
     rcode = launch_one<double, KK>(g, st, num_sms, sc, g->n, zc, qc, rc, stc, ws, ws_bytes, o, mode,   \
-                                   max_blocks, paper, z0c);                                            \
+                                   max_blocks, paper, z0c, grid_out);                                  \
   else                                                                                                 \
     rcode = launch_one<float, KK>(g, st, num_sms, sc, g->n, zc, qc, rc, stc, ws, ws_bytes, o, mode,    \
-                                  max_blocks, paper, z0c);
+                                  max_blocks, paper, z0c, grid_out);
     switch (K) {
       case 32: FJ_LAUNCH(32) break;
       case 16: FJ_LAUNCH(16) break;
@@ -895,9 +903,9 @@ extern "C" fj_status fj_solve_fixed(const fj_graph* g, void* stream, int32_t k, 
   FJ_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int) * 3 * 6, st));
   fj_opts od = o;
   od.flags = FJ_DEVICE_PTRS;
-  int done = 0;
+  int done = 0, grid = 0;
   rc = fj_solve_device(g, st, num_sms, k, s, z, dq, dres, dstat, base + head, FJ_FIXED_SCRATCH_BYTES - head, od,
-                       &done, 0, nullptr);
+                       &done, 0, nullptr, &grid);
   if (rc != FJ_OK) return rc;
   double hq[32 * 5], hres[32];
   int hstat[3 * 6];
@@ -931,6 +939,7 @@ extern "C" fj_status fj_solve_fixed(const fj_graph* g, void* stream, int32_t k, 
     info->rel_residual = worst;
     info->status = rc;
     info->columns = k;
+    info->blocks = grid;
   }
   return rc;
 }

@@ -36,6 +36,7 @@ PREC_FP64 = 1
 PREC_FP32 = 2
 
 QUANTITY_NAMES = ("C_I", "D", "P", "C", "I_dc")
+FJ_TUNE_MAX = 16
 
 
 class FJError(RuntimeError):
@@ -53,7 +54,8 @@ class Opts(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("device_ms", ctypes.c_double),
-                ("status", ctypes.c_int32), ("columns", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("columns", ctypes.c_int32),
+                ("blocks", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -61,6 +63,11 @@ class Info(ctypes.Structure):
 
 class Quant(ctypes.Structure):
     _fields_ = [(name, ctypes.c_double) for name in QUANTITY_NAMES]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("best", ctypes.c_int32), ("count", ctypes.c_int32),
+                ("blocks", ctypes.c_int32 * FJ_TUNE_MAX), ("ms", ctypes.c_double * FJ_TUNE_MAX)]
 
 
 _P = ctypes.c_void_p
@@ -73,6 +80,7 @@ _SIGNATURES = {
     "fj_destroy": (ctypes.c_int32, [_P]),
     "fj_set_stream": (ctypes.c_int32, [_P, _P]),
     "fj_set_max_blocks": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "fj_set_grid": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "fj_graph_upload": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
                                          ctypes.c_uint32, ctypes.POINTER(_P)]),
     "fj_graph_free": (ctypes.c_int32, [_P, _P]),
@@ -96,6 +104,8 @@ _SIGNATURES = {
                                          ctypes.c_int32, _P, ctypes.POINTER(Opts),
                                          ctypes.POINTER(ctypes.c_uint64)]),
     "fj_poll": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.c_int32, _P, ctypes.POINTER(Info)]),
+    "fj_tune": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, ctypes.POINTER(Opts), ctypes.c_int32,
+                                 ctypes.POINTER(TuneResult)]),
 }
 
 _lib = None
@@ -207,6 +217,10 @@ class Context:
     def set_max_blocks(self, nblocks: int):
         _check(load().fj_set_max_blocks(self.handle, int(nblocks)), "fj_set_max_blocks")
 
+    def set_grid(self, nblocks: int):
+        """fj_set_grid: later solves run on exactly nblocks blocks (0: default)."""
+        _check(load().fj_set_grid(self.handle, int(nblocks)), "fj_set_grid")
+
     # ------------------------------------------------------------- graphs
     def upload(self, n, src, dst, w=None, merge_duplicates=False) -> Graph:
         """Edge list -> device CSR.  numpy arrays (host) or torch CUDA tensors
@@ -317,6 +331,38 @@ class Context:
     def quantities(self, graph: Graph, s, opts: Opts | None = None):
         _, q, info = self.solve(graph, s, want_z=False, want_quant=True, opts=opts)
         return q, info
+
+    def tune(self, graph: Graph, s, opts: Opts | None = None, repeats: int = 3):
+        """fj_tune: time the solve of s on graph under each candidate grid and
+        keep the fastest for later solves of as many columns in the same
+        precision class.  s as for solve().  Returns {"best": blocks (0 =
+        default sizing), "grids": [(blocks, median ms), ...]}."""
+        lib = load()
+        o = Opts()
+        lib.fj_default_opts(ctypes.byref(o))
+        if opts is not None:
+            o = Opts(opts.tol, opts.inner_tol, opts.precision, opts.max_iter,
+                     opts.max_refine, opts.flags)
+        n = graph.stats()["n"]
+        if _is_torch_cuda(s):
+            import torch
+            k = 1 if s.dim() == 1 else int(s.shape[0])
+            if not s.is_contiguous() or s.dtype != torch.float64 or s.numel() != n * k:
+                raise ValueError("device s must be contiguous float64 with n*k elements")
+            keep, sp = s, s.data_ptr()
+            o.flags = (o.flags & ~FJ_DEVICE_PTRS) | FJ_DEVICE_PTRS
+        else:
+            sf = np.asfortranarray(np.asarray(s, dtype=np.float64).reshape(n, -1))
+            k = sf.shape[1]
+            keep, sp = sf, sf.ctypes.data
+            o.flags = (o.flags & ~FJ_DEVICE_PTRS) | FJ_HOST_PTRS
+        res = TuneResult()
+        rc = lib.fj_tune(self.handle, graph.handle, k, _P(sp), ctypes.byref(o), int(repeats),
+                         ctypes.byref(res))
+        del keep
+        _check(rc, "fj_tune")
+        return {"best": res.best,
+                "grids": [(res.blocks[i], res.ms[i]) for i in range(res.count)]}
 
 
 class Ticket:

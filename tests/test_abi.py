@@ -81,3 +81,26 @@ def test_new_entry_points_reject_null_arguments_without_a_device():
     info = fj.Info()
     assert lib.fj_solve_warm(None, None, 1, None, None, None, None, None, C.byref(info)) == fj.FJ_ERR_ARG
     assert b"z0" in lib.fj_last_error()
+
+
+def test_tune_layout_and_null_arguments_without_a_device():
+    import ctypes as C
+    text = open(os.path.join(ROOT, "include", "fj.h")).read()
+    assert int(re.search(r"#define FJ_TUNE_MAX (\d+)", text).group(1)) == fj.FJ_TUNE_MAX
+    # int32 best, int32 count, int32[16] blocks, then double[16] ms at offset 72
+    assert C.sizeof(fj.TuneResult) == 72 + 8 * fj.FJ_TUNE_MAX
+    assert fj.TuneResult.ms.offset == 72
+    lib = fj.load()
+    res = fj.TuneResult()
+    assert lib.fj_tune(None, None, 1, None, None, 3, C.byref(res)) == fj.FJ_ERR_ARG
+    assert b"non-NULL" in lib.fj_last_error()
+    assert lib.fj_tune(None, None, 1, None, None, 0, C.byref(res)) == fj.FJ_ERR_ARG
+
+
+def test_info_layout_and_set_grid_arguments_without_a_device():
+    import ctypes as C
+    # int32 x2, double x2, int32 status, columns, blocks (padded to 8 bytes)
+    assert fj.Info.blocks.offset == 32 and C.sizeof(fj.Info) == 40
+    lib = fj.load()
+    assert lib.fj_set_grid(None, 4) == fj.FJ_ERR_ARG
+    assert b"fj_set_grid" in lib.fj_last_error()

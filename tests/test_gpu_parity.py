@@ -148,6 +148,69 @@ def test_launch_shapes_agree_wide(ctx, blocks):
     np.testing.assert_allclose(z, zo, atol=1e-8)
 
 
+@pytest.mark.parametrize("grid", [1, 7, "2*SMs"])
+@pytest.mark.parametrize("k", [1, 16])
+def test_exact_grids(ctx, grid, k):
+    """fj_set_grid runs the solve on exactly the given grid, including many
+    more blocks than the work sizing picks (22 here), where most warps get no
+    work unit; results match the oracle."""
+    import torch
+    g = synth.chung_lu(20_000, 80_000, 2.3, seed=8, weighted=True)
+    s = synth.opinions_uniform(g.n, k, 4)
+    zo, qo = _oracle(g, s)
+    if grid == "2*SMs":
+        grid = 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    ctx.set_grid(grid)
+    try:
+        with ctx.upload_edges(g) as dg:
+            z, q, info = ctx.solve(dg, s)
+    finally:
+        ctx.set_grid(0)
+    assert info["blocks"] == grid
+    for j in range(k):
+        _check_quantities(q[j], qo[j], s[:, j], 1e-6)
+    np.testing.assert_allclose(z, zo, atol=1e-8)
+
+
+@pytest.mark.parametrize("k,prec", [(1, 1), (4, 0), (16, 0)])
+def test_grid_tuner(ctx, k, prec):
+    """fj_tune times the default sizing and grids of 2*SMs, SMs, ..., 1
+    blocks, keeps the fastest, and later solves of as many columns in the
+    same precision class run on it (the same bits as a solve on that grid
+    set by hand); other column counts keep the default sizing; results match
+    the oracle."""
+    from paper_2101_08143_gb300 import fj
+    g = synth.chung_lu(20_000, 80_000, 2.3, seed=8, weighted=True)
+    s = synth.opinions_uniform(g.n, k, 4)
+    s_other = synth.opinions_uniform(g.n, k + 1, 5)
+    zo, qo = _oracle(g, s)
+    opts = fj.default_opts(precision=prec)
+    with ctx.upload_edges(g) as dg:
+        _, _, info0 = ctx.solve(dg, s, opts=opts)
+        _, _, info_other0 = ctx.solve(dg, s_other, opts=opts)
+        res = ctx.tune(dg, s, opts=opts, repeats=2)
+        grids = [b for b, _ in res["grids"]]
+        times = dict(res["grids"])
+        assert grids[0] == 0 and grids[-1] == 1 and grids[1:] == sorted(grids[1:], reverse=True)
+        assert all(ms > 0 for ms in times.values())
+        assert times[res["best"]] == min(times.values())
+        z_t, q_t, info_t = ctx.solve(dg, s, opts=opts)
+        assert info_t["blocks"] == (res["best"] or info0["blocks"])
+        _, _, info_other = ctx.solve(dg, s_other, opts=opts)
+        assert info_other["blocks"] == info_other0["blocks"]
+        ctx.set_grid(info_t["blocks"])
+        try:
+            z_e, q_e, _ = ctx.solve(dg, s, opts=opts)
+        finally:
+            ctx.set_grid(0)
+        with pytest.raises(fj.FJError):
+            ctx.tune(dg, s, opts=fj.default_opts(flags=fj.FJ_TWO_SOLVES))
+    assert np.array_equal(z_t, z_e) and q_t == q_e
+    for j in range(k):
+        _check_quantities(q_t[j], qo[j], s[:, j], 1e-6)
+    np.testing.assert_allclose(z_t, zo, atol=1e-8)
+
+
 @pytest.mark.parametrize("k", [2, 40])
 def test_deterministic_bits(ctx, k):
     """Repeated solves, and solves on a re-uploaded graph, give the same bits;
