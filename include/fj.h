@@ -108,7 +108,12 @@ typedef struct fj_info {
   int32_t status;      /* same as the return value of the call               */
   int32_t columns;     /* k                                                  */
   int32_t blocks;      /* thread blocks of the solve's grid (largest launch)  */
+  uint32_t warnings;   /* FJ_WARN_* bits (conditions that are not errors)    */
 } fj_info;
+
+/* fj_info.warnings: some s_i lies outside [0, 1], the range Sec. 2.2
+ * assumes.  The solve and the quantities are computed all the same. */
+#define FJ_WARN_OPINION_RANGE 1u
 
 /* The five quantities of one opinion vector (Sec. 3.2 definitions). */
 typedef struct fj_quant {
@@ -210,7 +215,8 @@ fj_status fj_graph_stats(const fj_graph* g, int64_t* n, int64_t* nnz,
  *   opts  options (NULL: defaults); opts->flags says where s and z live
  *   info  optional host output
  * Any finite s is accepted (the paper assumes s in [0,1]; the algebra does
- * not need it).  Errors: FJ_ERR_ARG, FJ_ERR_OOM, FJ_ERR_NOT_CONVERGED (z and
+ * not need it); values outside [0, 1] set FJ_WARN_OPINION_RANGE in
+ * info->warnings.  Errors: FJ_ERR_ARG, FJ_ERR_OOM, FJ_ERR_NOT_CONVERGED (z and
  * quant still hold the last iterate), FJ_ERR_NUMERIC, FJ_ERR_TIMEOUT,
  * FJ_ERR_CUDA. */
 fj_status fj_solve_ex(fj_ctx* ctx, const fj_graph* g, int32_t k,

@@ -543,6 +543,7 @@ static fj_status solve_impl(fj_ctx* c, const fj_graph* g, int32_t k, const doubl
     info->status = rc;
     info->columns = k;
     info->blocks = grid_used;
+    info->warnings = (bits & kWarnOpinionRange) ? FJ_WARN_OPINION_RANGE : 0u;
   }
   return rc;
 }

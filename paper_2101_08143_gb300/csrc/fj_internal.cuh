@@ -46,6 +46,7 @@ enum : int {
   kErrNumeric = 8,
   kErrNotConverged = 16,
   kErrDuplicate = 32,
+  kWarnOpinionRange = 64,  // not an error: some s_i outside [0, 1]
 };
 
 struct Barrier {

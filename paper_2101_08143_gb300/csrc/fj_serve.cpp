@@ -269,6 +269,7 @@ void collect(Server& S, Request* r) {
   r->info.iterations = iters;
   r->info.refinements = refines;
   r->info.rel_residual = worst;
+  r->info.warnings = (bits & kWarnOpinionRange) ? FJ_WARN_OPINION_RANGE : 0u;
   r->info.device_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - r->t_start).count();
   if (r->own_graph) {

@@ -286,8 +286,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
 
   // ---------------------------------------------------------------- setup
   {
+    // the opinions' sum, and whether any lies outside the [0, 1] of Sec. 2.2
     double acc = 0.0;
-    for (int64_t idx = gtid; idx < NK; idx += gstride) acc += P.s[(int64_t)(c >> P.col_shift) * P.ld + idx / K];
+    bool outside = false;
+    for (int64_t idx = gtid; idx < NK; idx += gstride) {
+      const double x = P.s[(int64_t)(c >> P.col_shift) * P.ld + idx / K];
+      acc += x;
+      outside |= !(x >= 0.0 && x <= 1.0);
+    }
+    if (__syncthreads_or(outside) && threadIdx.x == 0) atomicOr(status, kWarnOpinionRange);
     const double v[1] = {acc};
     const int sl[1] = {S_SUM};
     block_store<K, 1>(v, sl, P.part, red);
@@ -940,6 +947,7 @@ extern "C" fj_status fj_solve_fixed(const fj_graph* g, void* stream, int32_t k, 
     info->status = rc;
     info->columns = k;
     info->blocks = grid;
+    info->warnings = (bits & kWarnOpinionRange) ? FJ_WARN_OPINION_RANGE : 0u;
   }
   return rc;
 }

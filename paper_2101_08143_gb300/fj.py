@@ -30,6 +30,7 @@ FJ_HOST_PTRS = 0
 FJ_DEVICE_PTRS = 1
 FJ_MERGE_DUPLICATES = 2
 FJ_TWO_SOLVES = 4
+FJ_WARN_OPINION_RANGE = 1
 
 PREC_MIXED = 0
 PREC_FP64 = 1
@@ -55,7 +56,7 @@ class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("device_ms", ctypes.c_double),
                 ("status", ctypes.c_int32), ("columns", ctypes.c_int32),
-                ("blocks", ctypes.c_int32)]
+                ("blocks", ctypes.c_int32), ("warnings", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

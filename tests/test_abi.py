@@ -99,8 +99,10 @@ def test_tune_layout_and_null_arguments_without_a_device():
 
 def test_info_layout_and_set_grid_arguments_without_a_device():
     import ctypes as C
-    # int32 x2, double x2, int32 status, columns, blocks (padded to 8 bytes)
-    assert fj.Info.blocks.offset == 32 and C.sizeof(fj.Info) == 40
+    # int32 x2, double x2, int32 status, columns, blocks, uint32 warnings
+    assert fj.Info.blocks.offset == 32 and fj.Info.warnings.offset == 36 and C.sizeof(fj.Info) == 40
+    text = open(os.path.join(ROOT, "include", "fj.h")).read()
+    assert int(re.search(r"#define FJ_WARN_OPINION_RANGE (\d+)u", text).group(1)) == fj.FJ_WARN_OPINION_RANGE
     lib = fj.load()
     assert lib.fj_set_grid(None, 4) == fj.FJ_ERR_ARG
     assert b"fj_set_grid" in lib.fj_last_error()

@@ -415,6 +415,50 @@ def test_two_solves_mode_rejected_where_unsupported(ctx):
 
 # ------------------------------------------------------------ edge cases
 
+def test_opinions_outside_the_unit_interval_warn(ctx):
+    """Any finite s is solved.  Opinions outside [0, 1], the range Sec. 2.2
+    assumes, set FJ_WARN_OPINION_RANGE in the info of the direct and the
+    served solve; in-range opinions leave it clear; results match the
+    oracle either way."""
+    from paper_2101_08143_gb300 import fj
+    g = synth.chung_lu(5_000, 20_000, 2.3, seed=3, weighted=True)
+    s_in = synth.opinions_uniform(g.n, 2, 7)
+    s_out = s_in.copy()
+    s_out[:, 1] = 3.0 * s_in[:, 1] - 1.0  # second column in [-1, 2]
+    zo, qo = _oracle(g, s_out)
+    with ctx.upload_edges(g) as dg:
+        _, _, info_in = ctx.solve(dg, s_in)
+        z, q, info_out = ctx.solve(dg, s_out)
+        t = fj.submit(ctx, dg, s_out)
+        rc, q_srv, info_srv = fj.poll(ctx, t, timeout_us=30_000_000)
+    assert info_in["warnings"] == 0
+    assert info_out["warnings"] == fj.FJ_WARN_OPINION_RANGE
+    assert rc == fj.FJ_OK and info_srv["warnings"] == fj.FJ_WARN_OPINION_RANGE
+    for j in range(2):
+        _check_quantities(q[j], qo[j], s_out[:, j], 1e-6)
+        _check_quantities(q_srv[j], qo[j], s_out[:, j], 1e-6)
+    np.testing.assert_allclose(z, zo, atol=1e-8)
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_non_finite_opinions_are_a_numeric_error(ctx, bad):
+    """A NaN or infinite s_i makes the float64 residual non-finite at the
+    first check: every block sees the same reduced value, stops, and the call
+    returns FJ_ERR_NUMERIC."""
+    from paper_2101_08143_gb300 import fj
+    g = synth.chung_lu(5_000, 20_000, 2.3, seed=3, weighted=True)
+    s = synth.opinions_uniform(g.n, 1, 7)[:, 0].copy()
+    s[123] = bad
+    with ctx.upload_edges(g) as dg:
+        with pytest.raises(fj.FJError) as e:
+            ctx.solve(dg, s)
+        assert e.value.code == fj.FJ_ERR_NUMERIC
+        # the context stays usable
+        s[123] = 0.5
+        _, q, info = ctx.solve(dg, s)
+    assert info["rc"] == fj.FJ_OK
+
+
 def test_edgeless_graph(ctx):
     g = synth.edgeless(1000)
     s = synth.opinions_uniform(1000, 1, 1)[:, 0]
