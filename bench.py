@@ -340,12 +340,12 @@ def small_graph_run(ctx, fj, torch, stream, reps=200):
     return out
 
 
-def serving_run(ctx, fj, n_requests=240, seed=4, rate_frac=0.5):
+def serving_run(ctx, fj, n_requests=240, seed=4, rate_fracs=(0.5, 0.8)):
     """A Poisson stream of requests that bring their own graph (Erdos-Renyi or
     Chung-Lu, n log-uniform in [10^3, 10^5], average degree U[4, 20],
     weights U(0,1], 1-16 opinion vectors) through fj_submit_edges / fj_poll.
-    First the saturation throughput (all requests at once), then an open
-    loop at rate_frac of it; latency = submit to completion.  The generated
+    First the saturation throughput (all requests at once), then open loops
+    at each of rate_fracs of it; latency = submit to completion.  The generated
     graphs are simple, so requests pass FJ_MERGE_DUPLICATES.  All requests
     are prepared before the clock starts; submitting one still copies its
     edge list and opinions (the API copies inputs at the call)."""
@@ -400,12 +400,18 @@ def serving_run(ctx, fj, n_requests=240, seed=4, rate_frac=0.5):
     run(None)  # warm-up
     lat, span, cols = run(None)
     sat = len(reqs) / span
-    arrivals = np.cumsum(rng.exponential(1.0 / (rate_frac * sat), len(reqs)))
-    lat2, span2, _ = run(arrivals)
+    loops = {}
+    for frac in rate_fracs:
+        arrivals = np.cumsum(rng.exponential(1.0 / (frac * sat), len(reqs)))
+        lat2, _, _ = run(arrivals)
+        loops[f"{frac:g}"] = {"rate_per_s": frac * sat,
+                              "latency_ms": {"p50": float(np.percentile(lat2, 50)),
+                                             "p99": float(np.percentile(lat2, 99))}}
+    first = loops[f"{rate_fracs[0]:g}"]
     return {"requests": len(reqs), "graph_pool": len(pool),
             "saturation_requests_per_s": sat, "saturation_column_solves_per_s": cols / span,
-            "open_loop_rate_per_s": rate_frac * sat,
-            "latency_ms": {"p50": float(np.percentile(lat2, 50)), "p99": float(np.percentile(lat2, 99))},
+            "open_loop_rate_per_s": first["rate_per_s"], "latency_ms": first["latency_ms"],
+            "open_loops_by_fraction_of_saturation": loops,
             "saturated_latency_ms": {"p50": float(np.percentile(lat, 50)),
                                      "p99": float(np.percentile(lat, 99))}}
 

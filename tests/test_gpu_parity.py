@@ -79,6 +79,32 @@ def test_erdos_renyi_2k(ctx, prec):
     assert info["iterations"] > 0
 
 
+def test_bench_workload_full_size(ctx):
+    """The benchmark's own workload and launch configuration: Chung-Lu
+    n = 1,000,000, m = 5,000,000, exponent 2.3, weights U(0,1], one
+    s ~ U[0,1]; device-pointer upload with FJ_MERGE_DUPLICATES, mixed
+    precision to relative residual 1e-8 on the full grid.  Every z_i is
+    compared with the oracle's float64 solve.  Since I + L has no eigenvalue
+    below 1, ||z - z*|| <= ||s_bar - (I + L) q|| <= 1e-8 ||s_bar||, which bounds
+    each element; the five quantities match to 1e-6."""
+    import torch
+    from paper_2101_08143_gb300 import fj
+    spec = synth.WORKLOADS["cl_n1m_m5m_b2.3"]
+    g = synth.make_graph(spec)
+    s = synth.make_opinions(spec, g.n)[:, 0]
+    zo, qo = _oracle(g, s)
+    dev = torch.device("cuda")
+    with ctx.upload(g.n, torch.from_numpy(g.src).to(dev), torch.from_numpy(g.dst).to(dev),
+                    torch.from_numpy(g.w).to(dev), merge_duplicates=True) as dg:
+        assert dg.stats()["nnz"] == 2 * g.m
+        z, q, info = ctx.solve(dg, torch.from_numpy(s).to(dev),
+                               opts=fj.default_opts(tol=1e-8, precision=fj.PREC_MIXED))
+    assert info["rel_residual"] <= 1e-8
+    bound = 1e-8 * float(np.linalg.norm(s - s.mean()))
+    assert float(np.max(np.abs(z.cpu().numpy() - zo[:, 0]))) <= bound
+    _check_quantities(q[0], qo[0], s, 1e-6)
+
+
 @pytest.mark.parametrize("n,m,weighted,seed", [(300, 900, True, 1), (1000, 20000, True, 2),
                                                (4097, 9000, False, 3), (12345, 60000, True, 4)])
 def test_random_graphs_several_tiles(ctx, n, m, weighted, seed):
