@@ -395,6 +395,68 @@ def test_planted_mistakes_are_caught(monkeypatch):
     assert pins_pass()
 
 
+def _planted(name):
+    """A plausible slip in the oracle, as a (function name, replacement)
+    pair for monkeypatching."""
+    orig_apply = fo.apply_laplacian
+    orig_from_z = fo.quantities_from_z
+    if name == "weights squared in L x":
+        return "apply_laplacian", lambda n, src, dst, w, x: orig_apply(
+            n, src, dst, None if w is None else np.asarray(w, dtype=np.float64) ** 2, x)
+    if name == "weights of the wrong edges in L x":
+        return "apply_laplacian", lambda n, src, dst, w, x: orig_apply(
+            n, src, dst, None if w is None else np.asarray(w)[::-1].copy(), x)
+    if name == "D over both directions":
+        def f(n, src, dst, w, s_, z):
+            q = dict(orig_from_z(n, src, dst, w, s_, z))
+            q["D"] *= 2
+            q["I_dc"] = q["D"] + q["C"]
+            return q
+        return "quantities_from_z", f
+    if name == "C_I against s_bar":
+        def f(n, src, dst, w, s_, z):
+            q = dict(orig_from_z(n, src, dst, w, s_, z))
+            q["C_I"] = float(np.sum((np.asarray(z) - fo.centred(s_)) ** 2))
+            return q
+        return "quantities_from_z", f
+    if name == "P without centring z":
+        def f(n, src, dst, w, s_, z):
+            q = dict(orig_from_z(n, src, dst, w, s_, z))
+            q["P"] = q["C"]
+            return q
+        return "quantities_from_z", f
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["weights squared in L x", "weights of the wrong edges in L x",
+                                  "D over both directions", "C_I against s_bar",
+                                  "P without centring z"])
+def test_more_planted_mistakes_are_caught(monkeypatch, name):
+    """Further slips, each planted in the CG path (n = 250 > the dense limit)
+    or in the definitions: the identities or the dense Lemma PropA norms
+    reject every one."""
+    g = synth.erdos_renyi(250, 900, seed=6, weighted=True)
+    s = np.random.default_rng(3).random(250)
+
+    def pins_pass():
+        try:
+            q = fo.quantities(250, g.src, g.dst, g.w, s)[0]
+            _identities(250, g.src, g.dst, g.w, s, q, 1e-10)
+            other = fo.quantities_norms(250, g.src, g.dst, g.w, s)
+            for qn in fo.QUANTITY_NAMES:
+                assert other[qn] == pytest.approx(q[qn], rel=1e-10)
+            return True
+        except AssertionError:
+            return False
+
+    assert pins_pass()
+    attr, repl = _planted(name)
+    monkeypatch.setattr(fo, attr, repl)
+    assert not pins_pass()
+    monkeypatch.undo()
+    assert pins_pass()
+
+
 # ------------------------------------------------- largest connected component
 
 def _bfs_components(n, src, dst):
