@@ -3,7 +3,11 @@
 This module is the one piece shared by the CUDA path's tests/bench and the CPU
 oracle.  It holds no arithmetic of the method itself (no Laplacian, no solve,
 no quantity): it only draws edge lists and opinion vectors from seeded numpy
-generators (PCG64), so the same seed gives the same bytes on x86 and Arm.
+generators (PCG64), whose streams are the same on every platform.  The one
+floating-point step before a draw, the Chung-Lu CDF, could differ by an ulp
+between math libraries, which changes a draw only if a variate falls inside
+that ulp; each test and the benchmark generate their inputs on the machine
+that runs them.
 
 Graph model (Sec. 2.1 of the paper): undirected, simple, weighted, w_e > 0.
 Generators emit simple graphs (no self-loops, no duplicate pairs).
