@@ -107,6 +107,8 @@ _SIGNATURES = {
     "fj_poll": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.c_int32, _P, ctypes.POINTER(Info)]),
     "fj_tune": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, ctypes.POINTER(Opts), ctypes.c_int32,
                                  ctypes.POINTER(TuneResult)]),
+    "fj_solve_fixed": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, ctypes.POINTER(Opts),
+                                        ctypes.POINTER(Info)]),
 }
 
 _lib = None

@@ -106,3 +106,11 @@ def test_info_layout_and_set_grid_arguments_without_a_device():
     lib = fj.load()
     assert lib.fj_set_grid(None, 4) == fj.FJ_ERR_ARG
     assert b"fj_set_grid" in lib.fj_last_error()
+
+
+def test_binding_declares_every_header_function():
+    """The ctypes binding gives a prototype to every function of fj.h."""
+    text = open(os.path.join(ROOT, "include", "fj.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(fj_[a-z0-9_]+)\s*\(", text))
+    assert names and not (names - set(fj._SIGNATURES)), sorted(names - set(fj._SIGNATURES))
