@@ -12,11 +12,13 @@ that runs them.
 Graph model (Sec. 2.1 of the paper): undirected, simple, weighted, w_e > 0.
 Generators emit simple graphs (no self-loops, no duplicate pairs).
 
-* Erdos-Renyi G(n, m): pairs drawn uniformly, deduplicated until exactly m.
+* Erdos-Renyi G(n, m): pairs drawn uniformly, deduplicated until at least m
+  distinct pairs exist, then m of them kept at random.
 * Chung-Lu power law: node weights (i+1)^(-1/(beta-1)); both endpoints drawn
-  proportionally to them; self-loops and repeated pairs dropped; drawing is
-  repeated until m distinct edges exist; node ids are then permuted at random
-  so that hubs are not simply the lowest ids.
+  proportionally to them (inverse CDF through a guide table); self-loops and
+  repeated pairs dropped; drawing is repeated until at least m distinct edges
+  exist and m of them are kept at random; node ids are then permuted at
+  random so that hubs are not simply the lowest ids.
 * Edge weights: 1.0 (unit) or Uniform(0, 1] rounded to float32.  The float32
   values are the ground truth both sides read.
 * Opinions (Sec. 5, "Internal opinion distributions"): Uniform[0,1]; the
@@ -50,39 +52,55 @@ class EdgeList:
         return self.w.astype(np.float64)
 
 
-def _dedupe_in_order(u: np.ndarray, v: np.ndarray, n: int):
-    """Drop self-loops and repeated unordered pairs, keeping first occurrences
-    in draw order."""
+def _distinct_keys(u: np.ndarray, v: np.ndarray, n: int) -> np.ndarray:
+    """Sorted distinct keys lo * n + hi of the unordered pairs {u, v}, with
+    self-loops dropped."""
     keep = u != v
-    u, v = u[keep], v[keep]
-    lo = np.minimum(u, v).astype(np.int64)
-    hi = np.maximum(u, v).astype(np.int64)
+    lo = np.minimum(u[keep], v[keep]).astype(np.int64)
+    hi = np.maximum(u[keep], v[keep]).astype(np.int64)
     key = lo * n + hi
-    _, first = np.unique(key, return_index=True)
-    first.sort()
-    return u[first], v[first]
+    key.sort()
+    if key.shape[0] == 0:
+        return key
+    first = np.empty(key.shape[0], dtype=bool)
+    first[0] = True
+    np.not_equal(key[1:], key[:-1], out=first[1:])
+    return key[first]
 
 
 def _collect_edges(draw, n: int, m: int, rng: np.random.Generator):
-    """Draw candidate pairs with `draw(count)` until m distinct edges exist."""
-    us, vs = [], []
-    have = 0
-    u_all = np.empty(0, dtype=np.int64)
-    v_all = np.empty(0, dtype=np.int64)
+    """Draw candidate pairs with `draw(count)` until m distinct unordered pairs
+    exist, then keep m of them chosen uniformly at random, in random order
+    (each as (lower id, higher id))."""
+    keys = np.empty(0, dtype=np.int64)
     factor = 1.25
-    while have < m:
-        need = m - have
+    while keys.shape[0] < m:
+        need = m - keys.shape[0]
         cnt = max(1024, int(need * factor))
         u, v = draw(cnt)
-        us.append(u)
-        vs.append(v)
-        u_all = np.concatenate(us)
-        v_all = np.concatenate(vs)
-        u_all, v_all = _dedupe_in_order(u_all, v_all, n)
-        us, vs = [u_all], [v_all]
-        have = u_all.shape[0]
+        new = _distinct_keys(u, v, n)
+        keys = new if keys.shape[0] == 0 else np.union1d(keys, new)
         factor *= 1.5
-    return u_all[:m], v_all[:m]
+    keys = keys[rng.permutation(keys.shape[0])[:m]]
+    return keys // n, keys % n
+
+
+def _inverse_cdf(cdf: np.ndarray, guide: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """For each r in [0, 1): the smallest i with cdf[i] > r (what
+    np.searchsorted(cdf, r, side="right") returns), found from a guide table
+    (Chen and Asau, 1974): guide[b] is that index for r = b / len(guide), so
+    the search starts at most one bucket early and steps forward."""
+    M = guide.shape[0]
+    b = np.floor(r * M).astype(np.int64) - 1
+    np.clip(b, 0, M - 1, out=b)
+    i = guide[b]
+    last = cdf.shape[0] - 1
+    idx = np.nonzero(cdf[i] <= r)[0]
+    while idx.shape[0]:
+        i[idx] += 1
+        np.minimum(i, last, out=i)
+        idx = idx[(cdf[i[idx]] <= r[idx]) & (i[idx] < last)]
+    return i
 
 
 def _weights(rng: np.random.Generator, m: int, weighted: bool):
@@ -117,12 +135,13 @@ def chung_lu(n: int, m: int, exponent: float, seed: int,
     cdf = np.cumsum((np.arange(n, dtype=np.float64) + 1.0) ** (-a))
     cdf /= cdf[-1]
 
+    guide = np.searchsorted(cdf, np.arange(2 * n, dtype=np.float64) / (2 * n), side="right")
+    np.minimum(guide, n - 1, out=guide)
+
     def draw(cnt):
-        u = np.searchsorted(cdf, rng.random(cnt), side="right")
-        v = np.searchsorted(cdf, rng.random(cnt), side="right")
-        np.minimum(u, n - 1, out=u)
-        np.minimum(v, n - 1, out=v)
-        return u.astype(np.int64), v.astype(np.int64)
+        u = _inverse_cdf(cdf, guide, rng.random(cnt))
+        v = _inverse_cdf(cdf, guide, rng.random(cnt))
+        return u, v
 
     u, v = _collect_edges(draw, n, m, rng)
     perm = rng.permutation(n).astype(np.int64)
