@@ -20,7 +20,10 @@
  *   P = ||q||^2, C = ||q + mean(s) 1||^2, C_I = ||s_bar - q||^2,
  *   D = ||W^1/2 B q||^2, I_dc = D + C.
  * The solve is Jacobi-preconditioned conjugate gradients on the GPU, with
- * float32 inner iterations refined by float64 residuals (or all float64).
+ * float32 inner iterations refined by double-float residuals (or all
+ * float64).  Each right-hand side is first scaled by an exact power of two so
+ * that max |s_bar| lies in [1, 2); z and the quantities are scaled back, so
+ * results hold at every finite opinion scale.
  * The paper's accuracy parameter delta (Algorithm 1, first step) is replaced
  * by a relative-residual target ||s_bar - (I + L) q||_2 <= tol ||s_bar||_2.
  *
@@ -79,11 +82,14 @@ enum {
 
 /* Arithmetic of the solve (fj_opts.precision). */
 enum {
-  FJ_PREC_MIXED = 0, /* float32 PCG inner iterations, float64 residual
-                        refinement: results to `tol` like FP64 (default)     */
-  FJ_PREC_FP64 = 1,  /* float64 throughout: the plain reference solve        */
-  FJ_PREC_FP32 = 2   /* float32 PCG only; float64 used only for the final
-                        residual and the quantity sums                        */
+  FJ_PREC_MIXED = 0, /* float32 PCG inner iterations, refinement residuals,
+                        iterate and quantity sums in double-float (two
+                        float32, ~48-bit significand): results to `tol` like
+                        FP64 (default)                                       */
+  FJ_PREC_FP64 = 1,  /* float64 throughout (inner iterations, residuals,
+                        iterate, sums): the plain reference solve            */
+  FJ_PREC_FP32 = 2   /* float32 PCG only; double-float used only for the
+                        final residual and the quantity sums                 */
 };
 
 typedef struct fj_ctx fj_ctx;     /* device, stream, workspace               */
@@ -338,19 +344,33 @@ fj_status fj_poll(fj_ctx* ctx, uint64_t ticket, int32_t timeout_us,
  *   k       number of opinion vectors, 1 <= k <= 32
  *   s       DEVICE float64[n*k], column-major; z: DEVICE float64[n*k] or NULL
  *   quant   fj_quant[k] output in HOST memory, or NULL; info: optional
- * The first call on each device looks up the array's device address; make
- * that first call before capturing any stream into a CUDA graph.  All calls
- * on a device share the one array and leave the last call's contents in it
- * (the solver clears what it needs zeroed): calls whose GPU work overlaps in
- * time race on it, so run them one after another (same stream, or
- * synchronized).  The call returns when its results are written.
- * Errors: FJ_ERR_ARG (NULL pointer, k out of range, or a solve whose scratch
- * exceeds FJ_FIXED_SCRATCH_BYTES; fj_solve_ex has no such limit), and the
- * solve errors of fj_solve_ex. */
+ * The first call on each device looks up the array's device address.  All
+ * calls on a device share the one array and leave the last call's contents
+ * in it (the solver clears what it needs zeroed): calls whose GPU work
+ * overlaps in time race on it, so run them one after another (same stream,
+ * or synchronized).  The call blocks until its results are on the host (it
+ * ends with device-to-host copies and a stream synchronization), so it
+ * cannot be called while its stream is being captured into a CUDA graph.
+ * Errors: FJ_ERR_ARG (NULL pointer, k out of range, s or z not device memory
+ * of the graph's device, or a solve whose scratch exceeds
+ * FJ_FIXED_SCRATCH_BYTES; fj_solve_ex has no such limit), and the solve
+ * errors of fj_solve_ex. */
 #define FJ_FIXED_SCRATCH_BYTES (64u << 20)
 fj_status fj_solve_fixed(const fj_graph* g, void* stream, int32_t k,
                          const double* s, double* z, fj_quant* quant,
                          const fj_opts* opts, fj_info* info);
+
+/* ---------------------------------------------------------------------
+ * Failure-detection test hook.  The paper has no counterpart.  Every grid
+ * barrier of a solve waits at most a bounded time (4 s by default), after
+ * which the solve is abandoned with FJ_ERR_TIMEOUT and the context stays
+ * usable.  This call sets that limit for later solves in this process
+ * (wait_ns <= 0 restores the default; otherwise 1e5 <= wait_ns <= 6e10) and,
+ * for tests of the timeout path, makes block 0 of later multi-block solves
+ * skip its arrival at grid barrier number `withhold` (1 = the first; 0, the
+ * default, never), so that the other blocks' wait runs out.  Not for
+ * production use.  Errors: FJ_ERR_ARG. */
+fj_status fj_debug_barrier(int64_t wait_ns, int32_t withhold);
 
 #ifdef __cplusplus
 }

@@ -3,8 +3,11 @@
 // A df64 value is the unevaluated sum hi + lo of two float32 numbers with
 // |lo| <= ulp(hi)/2, about 48 bits of significand.  GB300 runs float64 at a
 // small fraction of its float32 rate, so the float64-accurate parts of the
-// solve (residuals, refined iterate, quantity sums) are computed with these
-// float32 sequences instead:
+// mixed-precision solve (residuals, refined iterate, quantity sums) are
+// computed with these float32 sequences instead.  A df64 has float32's
+// exponent range (normal numbers from about 1e-38 to 3e38); the solver keeps
+// its values near 1 by scaling each right-hand side by a power of two first.
+// The sequences:
 //   two_sum         Knuth's error-free sum (TAOCP vol. 2, 4.2.2)
 //   quick_two_sum   Dekker's fast two-sum for |a| >= |b| (Dekker 1971)
 //   exact product   p = a*b, e = fma(a, b, -p)  (Dekker's product via FMA)
@@ -107,6 +110,43 @@ __device__ __forceinline__ double to_double(df64 x) { return df_to_double(x); }
 __device__ __forceinline__ float mul_w(float d, float w) { return w * d; }
 __device__ __forceinline__ double mul_w(double d, float w) { return (double)w * d; }
 __device__ __forceinline__ df64 mul_w(df64 d, float w) { return df_mul_f(d, w); }
+
+// Refinement arithmetic per inner type: float32 inner iterations are refined
+// in double-float, float64 inner iterations in plain float64 (the FP64 mode
+// is float64 throughout).
+template <typename VI>
+struct Refine {
+  using type = df64;
+};
+template <>
+struct Refine<double> {
+  using type = double;
+};
+
+template <typename R>
+__device__ __forceinline__ R from_double(double x);
+template <>
+__device__ __forceinline__ double from_double<double>(double x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ df64 from_double<df64>(double x) {
+  return df_from_double(x);
+}
+
+// A refinement value rounded to the inner type.
+template <typename VI>
+__device__ __forceinline__ VI to_inner(df64 r) {
+  return (VI)r.hi + (VI)r.lo;
+}
+template <typename VI>
+__device__ __forceinline__ VI to_inner(double r) {
+  return (VI)r;
+}
+
+// q + e for a refined iterate q and an inner correction e.
+__device__ __forceinline__ df64 add_inner(df64 q, float e) { return df_add_f(q, e); }
+__device__ __forceinline__ double add_inner(double q, double e) { return q + e; }
 
 // Warp xor-shuffle for every value type of the walks.
 __device__ __forceinline__ float shfl_xor_v(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }

@@ -107,6 +107,56 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// Streaming loads and stores (the .cs cache operator: lines allocated with
+// evict-first priority in L1 and L2).  The SpMV walks stream the graph (col,
+// val: read once per walk) and gather the iterate x; streaming the graph and
+// the vectors of the update pass keeps the gathered rows of x, loaded and
+// stored normally, in L2 while everything else passes through.
+
+// Read-only data of the whole kernel (the graph): non-coherent path.
+__device__ __forceinline__ int32_t ld_ro(const int32_t* a) {
+  int32_t v;
+  asm volatile("ld.global.cs.nc.b32 %0, [%1];" : "=r"(v) : "l"(a));
+  return v;
+}
+__device__ __forceinline__ float ld_ro(const float* a) {
+  float v;
+  asm volatile("ld.global.cs.nc.f32 %0, [%1];" : "=f"(v) : "l"(a));
+  return v;
+}
+
+// Data written by the kernel itself (vectors): coherent loads and stores.
+__device__ __forceinline__ void ld_cs(const float* a, float& v) {
+  asm volatile("ld.global.cs.f32 %0, [%1];" : "=f"(v) : "l"(a));
+}
+__device__ __forceinline__ void ld_cs(const double* a, double& v) {
+  asm volatile("ld.global.cs.f64 %0, [%1];" : "=d"(v) : "l"(a));
+}
+__device__ __forceinline__ void ld_cs(const float2* a, float2& v) {
+  asm volatile("ld.global.cs.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(a));
+}
+__device__ __forceinline__ void ld_cs(const float4* a, float4& v) {
+  asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a));
+}
+__device__ __forceinline__ void ld_cs(const double2* a, double2& v) {
+  asm volatile("ld.global.cs.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(a));
+}
+template <typename T>
+__device__ __forceinline__ T ld_cs(const T* a) {
+  T v;
+  ld_cs(a, v);
+  return v;
+}
+__device__ __forceinline__ void st_cs(float* a, float v) {
+  asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cs(double* a, double v) {
+  asm volatile("st.global.cs.f64 [%0], %1;" ::"l"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_cs(float2* a, float2 v) {
+  asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+
 }  // namespace fj
 
 // ------------------------------------------------------------------- host

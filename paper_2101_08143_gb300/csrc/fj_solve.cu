@@ -4,13 +4,20 @@
 // One cooperative launch runs the whole solve for K right-hand sides:
 //
 //   setup     mu = 1^T s / n, s_bar = s - mu 1               (Alg. 1, step 2)
+//             and a power of two 2^-e per column with max |s_bar| 2^-e in
+//             [1, 2): the system is linear, so the solve runs on the scaled
+//             s_bar exactly and q, z and the quantities are scaled back
 //   refine    repeat: r64 = s_bar - (I+L) q        (float64 residual walk)
 //               inner Jacobi-PCG on (I+L) e = r64 in the inner precision,
 //               q += e                                 (iterative refinement)
 //   output    z = q + mu 1 (Omega 1 = 1, Sec. 2.2), and from the last
-//             residual pass: P = ||q||^2, C = ||q + mu 1||^2,
-//             C_I = ||s_bar - q||^2, D = 1/2 sum_CSR w (q_i - q_j)^2
-//             (= ||W^1/2 B q||^2, Lemma PropA), I_dc = D + C.
+//             residual pass: P = ||q||^2, C = ||q + mu 1||^2
+//             = P + 2 mu 1^T q + n mu^2, C_I = ||s_bar - q||^2,
+//             D = 1/2 sum_CSR w (q_i - q_j)^2 (= ||W^1/2 B q||^2,
+//             Lemma PropA), I_dc = D + C.
+//
+// The refinement ("float64") arithmetic is double-float for float32 inner
+// iterations and plain float64 for float64 inner iterations.
 //
 // The inner solver is the Chronopoulos-Gear form of preconditioned CG: both
 // inner products of an iteration come out of one grid-wide reduction, so an
@@ -23,6 +30,7 @@
 // blocks), and every block evaluates the same scalars, so control flow is
 // identical in all blocks and results are bit-reproducible.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -35,18 +43,19 @@ constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
 constexpr int kMaxBlocksPerSM = 4;
 constexpr int kMaxDevices = 64;
-constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s per barrier wait
 
 enum Slot {
   S_SUM = 0,  // column sums of s
-  S_BB,       // ||s_bar||^2
+  S_MAX,      // max s (max-reduced)
+  S_NMIN,     // -min s (max-reduced)
+  S_BB,       // ||s_bar||^2 (scaled)
   S_GAM,      // (r, u)
   S_RR,       // (r, r) inner
   S_UU,       // (u, u)
   S_EQ,       // 1/2 sum_CSR w (u_i - u_j)^2 times 2 (raw walk sum)
   S_RR64,     // ||r64||^2
   S_P,        // ||q||^2
-  S_C,        // ||q + mu||^2
+  S_QS,       // 1^T q
   S_CI,       // ||s_bar - q||^2
   S_D,        // raw walk sum of w (q_i - q_j)^2 over CSR entries
   NSLOT
@@ -56,10 +65,11 @@ enum Mode { kModeMixed = 0, kModeFP64 = 1, kModeFP32 = 2 };
 
 template <typename VI>
 struct SolveParams {
+  using VR = typename Refine<VI>::type;  // refinement arithmetic
   SellGraph sg;  // work units: long-row chunks and 32-row slices
   const int32_t* perm;  // solver node -> input id
   VI* hub_part;         // [n_chunks][K] chunk sums of multi-chunk rows
-  df64* hub_part64;
+  VR* hub_part64;
   double* quad_u;       // [n_units][K] edge sums per work unit (K >= 8)
   unsigned long long* unit_counter;  // next work unit of the wide walks
   const float* dinv;
@@ -70,10 +80,10 @@ struct SolveParams {
   double* quant;  // [K][5]
   double* resid;  // [K]
   int* status;    // [0] err bits, [1] iterations, [2] refinements
-  // row-major n x K workspace; the refinement state is double-float
-  df64* sbar;
-  df64* q;
-  df64* t64;
+  // row-major n x K workspace; the refinement state is in VR
+  VR* sbar;
+  VR* q;
+  VR* t64;
   VI* x;
   VI* r;
   VI* u;
@@ -94,6 +104,16 @@ struct SolveParams {
   int col_shift;
   // warm start: initial guess z0 (same layout as s) or null
   const double* z0;
+  // bounded waits: a grid barrier gives up after timeout_ns; withhold > 0
+  // makes block 0 skip its arrival at barrier number `withhold` (the
+  // failure-detection test's stuck block)
+  uint64_t timeout_ns;
+  unsigned withhold;
+  // rows of the walks' gathered vectors kept in L2 (loaded and stored
+  // normally while everything else is streamed): of the inner iterate u and
+  // of the refined iterate q
+  int32_t hot_inner;
+  int32_t hot_ref;
 };
 
 // Grid-wide barrier with a bounded wait.  The counter only grows: barrier
@@ -102,7 +122,8 @@ struct SolveParams {
 // before it by __syncthreads); the wait polls with acquire loads.  Returns
 // false once any block has given up (error bit kErrTimeout), after which every
 // later barrier returns at once so that all blocks leave the kernel.
-__device__ __forceinline__ bool grid_sync(Barrier* bar, int* status, unsigned& epoch) {
+__device__ __forceinline__ bool grid_sync(Barrier* bar, int* status, unsigned& epoch, uint64_t timeout_ns,
+                                          unsigned withhold) {
   __shared__ int ok_sh;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -110,13 +131,14 @@ __device__ __forceinline__ bool grid_sync(Barrier* bar, int* status, unsigned& e
     if (gridDim.x > 1 && ok) {
       ++epoch;
       const unsigned target = epoch * gridDim.x;
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+      if (!(epoch == withhold && blockIdx.x == 0))
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
       if (ld_acquire_u32(&bar->count) < target) {
         const uint64_t t0 = global_ns();
         unsigned spins = 0;
         while (ld_acquire_u32(&bar->count) < target) {
           if ((++spins & 255u) == 0) {
-            if ((ld_volatile_i32(status) & kErrTimeout) || global_ns() - t0 > kBarrierTimeoutNs) {
+            if ((ld_volatile_i32(status) & kErrTimeout) || global_ns() - t0 > timeout_ns) {
               atomicOr(status, kErrTimeout);
               ok = 0;
               break;
@@ -131,9 +153,9 @@ __device__ __forceinline__ bool grid_sync(Barrier* bar, int* status, unsigned& e
   return ok_sh != 0;
 }
 
-// Block-level sums of NS per-thread values (thread column c = tid % K),
-// stored as this block's partials for the given slots.
-template <int K, int NS>
+// Block-level sums (or maxima, kMax) of NS per-thread values (thread column
+// c = tid % K), stored as this block's partials for the given slots.
+template <int K, int NS, bool kMax = false>
 __device__ __forceinline__ void block_store(const double (&v)[NS], const int (&slots)[NS],
                                             double* part, double* red /*[NS][kWarps][K]*/) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -142,32 +164,44 @@ __device__ __forceinline__ void block_store(const double (&v)[NS], const int (&s
   for (int j = 0; j < NS; ++j) {
     double x = v[j];
 #pragma unroll
-    for (int off = 16; off >= K; off >>= 1) x += __shfl_xor_sync(kFull, x, off);
+    for (int off = 16; off >= K; off >>= 1) {
+      const double y = __shfl_xor_sync(kFull, x, off);
+      x = kMax ? fmax(x, y) : x + y;
+    }
     if (lane < K) red[(j * kWarps + warp) * K + lane] = x;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < NS * K; e += kThreads) {
     const int j = e / K, c = e % K;
-    double s = 0.0;
+    double s = kMax ? -INFINITY : 0.0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += red[(j * kWarps + w) * K + c];
+    for (int w = 0; w < kWarps; ++w) {
+      const double y = red[(j * kWarps + w) * K + c];
+      s = kMax ? fmax(s, y) : s + y;
+    }
     part[((int64_t)blockIdx.x * NSLOT + slots[j]) * K + c] = s;
   }
   __syncthreads();
 }
 
-// After a barrier: res[slot][c] = sum over blocks of the partials, in block
-// order, identically in every block.
-template <int K, int NS>
+// After a barrier: res[slot][c] = sum (or max, kMax) over blocks of the
+// partials, in block order, identically in every block.
+template <int K, int NS, bool kMax = false>
 __device__ __forceinline__ void grid_reduce(const int (&slots)[NS], const double* part,
                                             double* res /*[NSLOT][K]*/) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int e = warp; e < NS * K; e += kWarps) {
     const int slot = slots[e / K], c = e % K;
-    double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&part[((int64_t)b * NSLOT + slot) * K + c]);
+    double s = kMax ? -INFINITY : 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      const double y = __ldcg(&part[((int64_t)b * NSLOT + slot) * K + c]);
+      s = kMax ? fmax(s, y) : s + y;
+    }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+    for (int off = 16; off > 0; off >>= 1) {
+      const double y = __shfl_xor_sync(kFull, s, off);
+      s = kMax ? fmax(s, y) : s + y;
+    }
     if (lane == 0) res[slot * K + c] = s;
   }
   __syncthreads();
@@ -188,7 +222,7 @@ template <typename T, int K>
 __device__ __forceinline__ void wide_walk(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
                                           T* __restrict__ part,
                                           unsigned long long* counter, unsigned long long base,
-                                          double* __restrict__ quad_u, T* __restrict__ sxr) {
+                                          double* __restrict__ quad_u, T* __restrict__ sxr, int32_t hot) {
   const int lane = threadIdx.x & 31;
   while (true) {
     unsigned long long k = 0;
@@ -196,7 +230,7 @@ __device__ __forceinline__ void wide_walk(const SellGraph& g, const T* __restric
     const int64_t u = (int64_t)__shfl_sync(kFull, k, 0);
     if (u >= g.n_units) break;
     T q = num<T>(0.f);
-    wide_unit<T, K>(g, x, out, part, u, q, sxr);
+    wide_unit<T, K>(g, x, out, part, u, q, sxr, hot);
     double qd = to_double(q);
 #pragma unroll
     for (int off = K; off < 32; off <<= 1) qd += __shfl_xor_sync(kFull, qd, off);
@@ -236,10 +270,13 @@ __device__ __forceinline__ double lane_share(T (&v)[K]) {
 
 template <typename VI, int K>
 __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
+  using VR = typename SolveParams<VI>::VR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* red = reinterpret_cast<double*>(smem_raw);  // [7][kWarps][K], aliases the staging
   __shared__ double res[NSLOT * K];
   __shared__ double alpha[K], beta[K], gam_prev[K], alpha_prev[K], rr_goal[K], mu[K], bb[K];
+  __shared__ double sc[K], isc[K];  // 2^-e and 2^e of each column
+  __shared__ int ex[K];             // e
   __shared__ int active[K], first[K], done[K], inner_ok[K];
   __shared__ int ctl_any_active, ctl_stop;
 
@@ -251,10 +288,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   const int c = threadIdx.x % K;
   // per-warp staging of the wide walks' row values
   VI* my_sxr = reinterpret_cast<VI*>(smem_raw + warp * kWideStageBytes);
-  df64* my_sxr64 = reinterpret_cast<df64*>(my_sxr);
+  VR* my_sxr64 = reinterpret_cast<VR*>(my_sxr);
   int* status = P.status;
   const bool fp32_mode = P.mode == kModeFP32;
   unsigned epoch = 0;  // barriers passed (used by thread 0)
+  auto sync = [&]() { return grid_sync(P.bar, status, epoch, P.timeout_ns, P.withhold); };
   // every K walks the same work units (sliced ELL for K <= 4, lanes as
   // columns for K >= 8), so all row sums are complete after a walk
   constexpr bool kWide = K >= 8;
@@ -286,59 +324,77 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
 
   // ---------------------------------------------------------------- setup
   {
-    // the opinions' sum, and whether any lies outside the [0, 1] of Sec. 2.2
-    double acc = 0.0;
+    // the opinions' sum and range, and whether any lies outside the [0, 1]
+    // of Sec. 2.2
+    double acc = 0.0, mx = -INFINITY, nmn = -INFINITY;
     bool outside = false;
     for (int64_t idx = gtid; idx < NK; idx += gstride) {
       const double x = P.s[(int64_t)(c >> P.col_shift) * P.ld + idx / K];
       acc += x;
+      mx = fmax(mx, x);
+      nmn = fmax(nmn, -x);
       outside |= !(x >= 0.0 && x <= 1.0);
     }
     if (__syncthreads_or(outside) && threadIdx.x == 0) atomicOr(status, kWarnOpinionRange);
     const double v[1] = {acc};
     const int sl[1] = {S_SUM};
     block_store<K, 1>(v, sl, P.part, red);
+    const double vm[2] = {mx, nmn};
+    const int slm[2] = {S_MAX, S_NMIN};
+    block_store<K, 2, true>(vm, slm, P.part, red);
   }
-  if (!grid_sync(P.bar, status, epoch)) return;
+  if (!sync()) return;
   {
     const int sl[1] = {S_SUM};
     grid_reduce<K, 1>(sl, P.part, res);
+    const int slm[2] = {S_MAX, S_NMIN};
+    grid_reduce<K, 2, true>(slm, P.part, res);
     if (threadIdx.x < K) {
+      const int cc = threadIdx.x;
       // a column solved as is (two-solve mode, even columns) keeps mu = 0
-      mu[threadIdx.x] = (P.paper && !(threadIdx.x & 1)) ? 0.0 : res[S_SUM * K + threadIdx.x] / (double)n;
-      done[threadIdx.x] = 0;
+      const double m = (P.paper && !(cc & 1)) ? 0.0 : res[S_SUM * K + cc] / (double)n;
+      mu[cc] = m;
+      // max |s_bar| = max(max s - mu, mu - min s); its binary exponent e
+      // (clamped so that 2^-e and 2^e stay normal) scales the column
+      const double bound = fmax(res[S_MAX * K + cc] - m, res[S_NMIN * K + cc] + m);
+      int e = 0;
+      if (bound > 0.0 && isfinite(bound)) e = max(-1020, min(1020, ilogb(bound)));
+      ex[cc] = e;
+      sc[cc] = ldexp(1.0, -e);
+      isc[cc] = ldexp(1.0, e);
+      done[cc] = 0;
     }
     __syncthreads();
   }
 
-  // float64 residual walk: t64 = L q (off-diagonal part of (I + L) q) and
+  // refinement residual walk: t64 = L q (off-diagonal part of (I + L) q) and
   // this block's part of sum w (q_i - q_j)^2, then the barrier
   auto residual_walk = [&]() -> bool {
     double quad;
     if constexpr (kWide) {
-      wide_walk<df64, K>(P.sg, P.q, P.t64, P.hub_part64, P.unit_counter, unit_base, P.quad_u, my_sxr64);
+      wide_walk<VR, K>(P.sg, P.q, P.t64, P.hub_part64, P.unit_counter, unit_base, P.quad_u, my_sxr64, P.hot_ref);
       unit_base += unit_step;
-      if (!grid_sync(P.bar, status, epoch)) return false;
+      if (!sync()) return false;
       quad = unit_sum<K>(P.quad_u, u0, u1);
     } else {
-      df64 qd[K];
+      VR qd[K];
 #pragma unroll
-      for (int cc = 0; cc < K; ++cc) qd[cc] = df_from_float(0.0f);
-      sell_walk<df64, K, kResidBatch>(P.sg, P.q, P.t64, P.hub_part64, u0, u1, qd);
-      quad = lane_share<df64, K>(qd);
+      for (int cc = 0; cc < K; ++cc) qd[cc] = num<VR>(0.0f);
+      sell_walk<VR, K, kResidBatch>(P.sg, P.q, P.t64, P.hub_part64, u0, u1, qd, P.hot_ref);
+      quad = lane_share<VR, K>(qd);
     }
     const double v[1] = {quad};
     const int sl[1] = {S_D};
     block_store<K, 1>(v, sl, P.part, red);
-    return grid_sync(P.bar, status, epoch);
+    return sync();
   };
 
-  // warm start: q = z0 - mu 1 (its residual walk opens the loop)
+  // warm start: q = (z0 - mu 1) 2^-e (its residual walk opens the loop)
   const bool warm = P.z0 != nullptr;
   if (warm) {
     for (int64_t idx = gtid; idx < NK; idx += gstride)
-      P.q[idx] = df_from_double(P.z0[(int64_t)(c >> P.col_shift) * P.ld + P.perm[idx / K]] - mu[c]);
-    if (!grid_sync(P.bar, status, epoch)) return;
+      P.q[idx] = from_double<VR>((P.z0[(int64_t)(c >> P.col_shift) * P.ld + P.perm[idx / K]] - mu[c]) * sc[c]);
+    if (!sync()) return;
   }
 
   int iters = 0, refines = 0;
@@ -346,59 +402,60 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   bool need_walk = warm;  // q changed since the last residual walk
   while (true) {
     if (need_walk && !residual_walk()) return;
-    // ------------------------------------------------ float64 residual pass
+    // ---------------------------------------------- refinement residual pass
     // r64 = s_bar - q - t64 (t64 = off-diagonal part of L q, from the walk)
     // plus the quantity partials and the start of the next inner solve.
     {
-      // float64-accurate sums in double-float; the inner-solve sums in VI
-      const df64 z0 = df_from_float(0.0f);
-      df64 a_rr64 = z0, a_p = z0, a_c = z0, a_ci = z0;
+      // float64-accurate sums in VR; the inner-solve sums in VI
+      const VR zero = num<VR>(0.0f);
+      VR a_rr64 = zero, a_p = zero, a_qs = zero, a_ci = zero;
       double a_bb = 0, a_gam = 0, a_rr = 0, a_uu = 0;
-      const double m = mu[c];
-      const df64 mdf = df_from_double(m);
+      const double m = mu[c], scale = sc[c];
       const bool lz_col = P.paper && !(c & 1);
       for (int64_t idx = gtid; idx < NK; idx += gstride) {
         const int64_t i = idx / K;
-        df64 sb, qv, lq;
+        VR sb, qv, lq;
         if (init) {
-          const double sbd = P.s[(int64_t)(c >> P.col_shift) * P.ld + P.perm[i]] - m;
-          sb = df_from_double(sbd);
+          const double sbd = (P.s[(int64_t)(c >> P.col_shift) * P.ld + P.perm[i]] - m) * scale;
+          sb = from_double<VR>(sbd);
           P.sbar[idx] = sb;
           a_bb += sbd * sbd;
           if (warm) {
             qv = P.q[idx];
-            lq = row_t<df64, K>(P.sg, P.t64, P.hub_part64, i, idx, c);
+            lq = row_t<VR, K>(P.sg, P.t64, P.hub_part64, i, idx, c);
           } else {
-            P.q[idx] = z0;
-            qv = z0;
-            lq = z0;
+            P.q[idx] = zero;
+            qv = zero;
+            lq = zero;
           }
         } else {
           sb = P.sbar[idx];
           qv = P.q[idx];
-          lq = row_t<df64, K>(P.sg, P.t64, P.hub_part64, i, idx, c);
+          lq = row_t<VR, K>(P.sg, P.t64, P.hub_part64, i, idx, c);
         }
-        const df64 r64 = df_sub(df_sub(sb, qv), lq);
-        a_rr64 += df_mul(r64, r64);
-        a_p += df_mul(qv, qv);
-        const df64 zq = df_add(qv, mdf);
-        a_c += df_mul(zq, zq);
+        const VR r64 = (sb - qv) - lq;
+        a_rr64 += r64 * r64;
+        a_p += qv * qv;
+        a_qs += qv;
         // C_I = ||s_bar - q||^2, or ||L z~||^2 for a column solved as is
         // in two-solve mode (lq = off-diagonal part of (I + L) q = L q)
-        const df64 dq = lz_col ? lq : df_sub(sb, qv);
-        a_ci += df_mul(dq, dq);
-        const VI rv = (VI)r64.hi + (VI)r64.lo;
+        const VR dq = lz_col ? lq : sb - qv;
+        a_ci += dq * dq;
+        const VI rv = to_inner<VI>(r64);
         const VI uv = P.dinv[i] * rv;
-        P.x[idx] = VI(0);
-        P.r[idx] = rv;
-        P.u[idx] = uv;
+        st_cs(P.x + idx, VI(0));
+        st_cs(P.r + idx, rv);
+        if (i < P.hot_inner)
+          P.u[idx] = uv;
+        else
+          st_cs(P.u + idx, uv);
         a_gam += (double)(rv * uv);
         a_rr += (double)(rv * rv);
         a_uu += (double)(uv * uv);
       }
-      const double v[7] = {df_to_double(a_rr64), df_to_double(a_p), df_to_double(a_c), df_to_double(a_ci),
+      const double v[7] = {to_double(a_rr64), to_double(a_p), to_double(a_qs), to_double(a_ci),
                            a_gam, a_rr, a_uu};
-      const int sl[7] = {S_RR64, S_P, S_C, S_CI, S_GAM, S_RR, S_UU};
+      const int sl[7] = {S_RR64, S_P, S_QS, S_CI, S_GAM, S_RR, S_UU};
       block_store<K, 7>(v, sl, P.part, red);
       if (init) {
         const double vb[1] = {a_bb};
@@ -406,9 +463,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         block_store<K, 1>(vb, sb, P.part, red);
       }
     }
-    if (!grid_sync(P.bar, status, epoch)) return;
+    if (!sync()) return;
     {
-      const int sl[7] = {S_RR64, S_P, S_C, S_CI, S_GAM, S_RR, S_UU};
+      const int sl[7] = {S_RR64, S_P, S_QS, S_CI, S_GAM, S_RR, S_UU};
       grid_reduce<K, 7>(sl, P.part, res);
       if (init) {
         const int sb[1] = {S_BB};
@@ -427,13 +484,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       const double rr64 = res[S_RR64 * K + cc];
       const double rel = bb[cc] > 0.0 ? sqrt(rr64 / bb[cc]) : 0.0;
       if (!finite(rr64)) atomicOr(status, kErrNumeric);
-      // quantities of the current iterate (final after the last pass)
+      // quantities of the current iterate (final after the last pass),
+      // scaled back: squares by 2^2e, 1^T q by 2^e
       if (blockIdx.x == 0) {
-        const double D = (init && !warm) ? 0.0 : 0.5 * res[S_D * K + cc];
-        const double C = res[S_C * K + cc];
-        P.quant[cc * 5 + 0] = res[S_CI * K + cc];
+        const int e2 = 2 * ex[cc];
+        const double m = mu[cc];
+        const double D = (init && !warm) ? 0.0 : ldexp(0.5 * res[S_D * K + cc], e2);
+        const double Pq = ldexp(res[S_P * K + cc], e2);
+        const double C = Pq + 2.0 * m * ldexp(res[S_QS * K + cc], ex[cc]) + (double)n * m * m;
+        P.quant[cc * 5 + 0] = ldexp(res[S_CI * K + cc], e2);
         P.quant[cc * 5 + 1] = D;
-        P.quant[cc * 5 + 2] = res[S_P * K + cc];
+        P.quant[cc * 5 + 2] = Pq;
         P.quant[cc * 5 + 3] = C;
         P.quant[cc * 5 + 4] = D + C;
         P.resid[cc] = rel;
@@ -479,22 +540,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       {
         double qv;
         if constexpr (kWide) {
-          wide_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.unit_counter, unit_base, P.quad_u, my_sxr);
+          wide_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.unit_counter, unit_base, P.quad_u, my_sxr, P.hot_inner);
           unit_base += unit_step;
-          if (!grid_sync(P.bar, status, epoch)) return;
+          if (!sync()) return;
           qv = unit_sum<K>(P.quad_u, u0, u1);
         } else {
           VI quad[K];
 #pragma unroll
           for (int cc = 0; cc < K; ++cc) quad[cc] = VI(0);
-          sell_walk<VI, K, kInnerBatch>(P.sg, P.u, P.t, P.hub_part, u0, u1, quad);
+          sell_walk<VI, K, kInnerBatch>(P.sg, P.u, P.t, P.hub_part, u0, u1, quad, P.hot_inner);
           qv = lane_share<VI, K>(quad);
         }
         const double v[1] = {qv};
         const int sl[1] = {S_EQ};
         block_store<K, 1>(v, sl, P.part, red);
       }
-      if (!grid_sync(P.bar, status, epoch)) return;
+      if (!sync()) return;
       {
         const int sl[1] = {S_EQ};
         grid_reduce<K, 1>(sl, P.part, res);
@@ -543,6 +604,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         VI* __restrict__ vu = P.u;
         const VI* __restrict__ vt = P.t;
         const float* __restrict__ vdinv = P.dinv;
+        // the new u is the next walk's gathered vector: kept in L2 for rows
+        // below hot_inner, the other vectors streamed
+        const int64_t hot_idx = (int64_t)P.hot_inner * K;
         // kV elements per thread per round, all loads issued before use
         constexpr int kV = 2;
         for (int64_t base = gtid; base < NK; base += kV * gstride) {
@@ -552,13 +616,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
             const int64_t idx = base + e * gstride;
             if (idx < NK) {
               const int64_t i = idx / K;
-              uv[e] = vu[idx];
+              uv[e] = ld_cs(vu + idx);
               tv[e] = row_t<VI, K>(P.sg, vt, P.hub_part, i, idx, c);
-              pv[e] = fst ? VI(0) : vp[idx];
-              dv[e] = fst ? VI(0) : vd[idx];
-              xv[e] = vx[idx];
-              rv[e] = vr[idx];
-              di[e] = vdinv[i];
+              pv[e] = fst ? VI(0) : ld_cs(vp + idx);
+              dv[e] = fst ? VI(0) : ld_cs(vd + idx);
+              xv[e] = ld_cs(vx + idx);
+              rv[e] = ld_cs(vr + idx);
+              di[e] = ld_ro(vdinv + i);
             }
           }
 #pragma unroll
@@ -571,11 +635,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
               const VI xn = xv[e] + al * pn;
               const VI rn = rv[e] - al * dn;
               const VI un = di[e] * rn;
-              vp[idx] = pn;
-              vd[idx] = dn;
-              vx[idx] = xn;
-              vr[idx] = rn;
-              vu[idx] = un;
+              st_cs(vp + idx, pn);
+              st_cs(vd + idx, dn);
+              st_cs(vx + idx, xn);
+              st_cs(vr + idx, rn);
+              if (idx < hot_idx)
+                vu[idx] = un;
+              else
+                st_cs(vu + idx, un);
               l_gam += rn * un;
               l_rr += rn * rn;
               l_uu += un * un;
@@ -589,7 +656,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         const int sl[3] = {S_GAM, S_RR, S_UU};
         block_store<K, 3>(v, sl, P.part, red);
       }
-      if (!grid_sync(P.bar, status, epoch)) return;
+      if (!sync()) return;
       {
         const int sl[3] = {S_GAM, S_RR, S_UU};
         grid_reduce<K, 3>(sl, P.part, res);
@@ -618,22 +685,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       __syncthreads();
     }
 
-    // q += x (double-float), then the residual walk t64 = L q and
-    // sum w (q_i - q_j)^2
-    for (int64_t idx = gtid; idx < NK; idx += gstride) {
-      if constexpr (sizeof(VI) == 4)
-        P.q[idx] = df_add_f(P.q[idx], (float)P.x[idx]);
-      else
-        P.q[idx] = df_add(P.q[idx], df_from_double((double)P.x[idx]));
-    }
-    if (!grid_sync(P.bar, status, epoch)) return;
+    // q += x in the refinement arithmetic, then the residual walk t64 = L q
+    // and sum w (q_i - q_j)^2
+    for (int64_t idx = gtid; idx < NK; idx += gstride) P.q[idx] = add_inner(P.q[idx], P.x[idx]);
+    if (!sync()) return;
     need_walk = true;
   }
 
   // ---------------------------------------------------------------- output
   if (P.z_out && !(P.paper && (c & 1))) {
     for (int64_t idx = gtid; idx < NK; idx += gstride)
-      P.z_out[(int64_t)(c >> P.col_shift) * P.ld + P.perm[idx / K]] = df_to_double(P.q[idx]) + mu[c];
+      P.z_out[(int64_t)(c >> P.col_shift) * P.ld + P.perm[idx / K]] = to_double(P.q[idx]) * isc[c] + mu[c];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     int all_done = 1;
@@ -645,6 +707,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
 }
 
 // ------------------------------------------------------------------ host
+
+// Limit of every grid-barrier wait, and the test hook's withheld barrier
+// (fj_debug_barrier).
+constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // 4 s
+// Bytes of a walk's gathered vector kept in L2 (of 126 MB): the rows of the
+// highest degree, which most gathers hit, up to this size.
+constexpr int64_t kL2KeepBytes = 80ll << 20;
+std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};
+std::atomic<int> g_withhold{0};
 
 template <typename VI, int K>
 static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, const double* s,
@@ -714,9 +785,11 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.quant = quant;
   P.resid = resid;
   P.status = status;
-  P.sbar = (df64*)take(NK * 8);
-  P.q = (df64*)take(NK * 8);
-  P.t64 = (df64*)take(NK * 8);
+  using VR = typename SolveParams<VI>::VR;
+  static_assert(sizeof(VR) == 8, "refinement values are 8 bytes");
+  P.sbar = (VR*)take(NK * 8);
+  P.q = (VR*)take(NK * 8);
+  P.t64 = (VR*)take(NK * 8);
   P.x = (VI*)take(NK * sizeof(VI));
   P.r = (VI*)take(NK * sizeof(VI));
   P.u = (VI*)take(NK * sizeof(VI));
@@ -725,7 +798,7 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.t = (VI*)take(NK * sizeof(VI));
   P.part = (double*)take((size_t)blocks * NSLOT * K * 8);
   P.hub_part = (VI*)take(std::max<int64_t>(g->n_chunks, 1) * K * sizeof(VI));
-  P.hub_part64 = (df64*)take(std::max<int64_t>(g->n_chunks, 1) * K * 8);
+  P.hub_part64 = (VR*)take(std::max<int64_t>(g->n_chunks, 1) * K * 8);
   P.quad_u = (double*)take(std::max<int64_t>(g->n_units, 1) * K * 8);
   P.bar = (Barrier*)take(64);  // the barrier, then the unit counter
   P.unit_counter = (unsigned long long*)((char*)P.bar + 32);
@@ -741,6 +814,10 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.paper = paper ? 1 : 0;
   P.z0 = z0;
   P.col_shift = paper ? 1 : 0;
+  P.timeout_ns = g_wait_ns.load(std::memory_order_relaxed);
+  P.hot_inner = (int32_t)std::min<int64_t>(n, kL2KeepBytes / ((int64_t)K * (int64_t)sizeof(VI)));
+  P.hot_ref = (int32_t)std::min<int64_t>(n, kL2KeepBytes / ((int64_t)K * 8));
+  P.withhold = (unsigned)g_withhold.load(std::memory_order_relaxed);
   FJ_CUDA(cudaMemsetAsync(P.bar, 0, 64, st));
   void* args[] = {&P};
   FJ_CUDA(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(kThreads), args, dyn, st));
@@ -751,6 +828,18 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
 }  // namespace fj
 
 using namespace fj;
+
+// Failure-detection test hook: the limit of later solves' barrier waits, and
+// a barrier at which block 0 of later multi-block solves does not arrive.
+extern "C" fj_status fj_debug_barrier(int64_t wait_ns, int32_t withhold) {
+  if (wait_ns > 60000000000ll || (wait_ns > 0 && wait_ns < 100000) || withhold < 0) {
+    set_error("fj_debug_barrier: need wait_ns <= 0 (default) or in [1e5, 6e10], withhold >= 0");
+    return FJ_ERR_ARG;
+  }
+  g_wait_ns.store(wait_ns > 0 ? (uint64_t)wait_ns : kDefaultWaitNs, std::memory_order_relaxed);
+  g_withhold.store(withhold, std::memory_order_relaxed);
+  return FJ_OK;
+}
 
 // Workspace bytes one launch of K columns needs.
 size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms) {
@@ -878,6 +967,21 @@ extern "C" fj_status fj_solve_fixed(const fj_graph* g, void* stream, int32_t k, 
     return FJ_ERR_ARG;
   }
   FJ_CUDA(cudaSetDevice(g->device));
+  // s and z are read and written by the kernel directly: they must be device
+  // (or managed) memory of the graph's device (the query allocates nothing)
+  for (const void* ptr : {(const void*)s, (const void*)z}) {
+    if (!ptr) continue;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+      cudaGetLastError();
+      a.type = cudaMemoryTypeUnregistered;
+    }
+    if (!((a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == g->device)) {
+      set_error("fj_solve_fixed: s and z must be device memory of device %d (opts->flags is ignored)",
+                g->device);
+      return FJ_ERR_ARG;
+    }
+  }
   int num_sms = 0;
   FJ_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, g->device));
   // launches of 32/16/8/4/2/1 columns, as in fj_solve_ex

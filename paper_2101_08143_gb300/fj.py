@@ -109,6 +109,7 @@ _SIGNATURES = {
                                  ctypes.POINTER(TuneResult)]),
     "fj_solve_fixed": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, ctypes.POINTER(Opts),
                                         ctypes.POINTER(Info)]),
+    "fj_debug_barrier": (ctypes.c_int32, [ctypes.c_int64, ctypes.c_int32]),
 }
 
 _lib = None
