@@ -115,6 +115,12 @@ typedef struct fj_info {
   int32_t columns;     /* k                                                  */
   int32_t blocks;      /* thread blocks of the solve's grid (largest launch)  */
   uint32_t warnings;   /* FJ_WARN_* bits (conditions that are not errors)    */
+  double t_begin_ms;   /* served requests (fj_poll): device time, in ms since
+                          the serving worker started, when the request was
+                          admitted (its first GPU work) ...                  */
+  double t_end_ms;     /* ... and when its last GPU work ended; 0 otherwise  */
+  int32_t batched;     /* served requests: 1 if it ran in a packed batch      */
+  int32_t reserved;
 } fj_info;
 
 /* fj_info.warnings: some s_i lies outside [0, 1], the range Sec. 2.2
@@ -189,6 +195,26 @@ fj_status fj_set_grid(fj_ctx* ctx, int32_t blocks);
 fj_status fj_graph_upload(fj_ctx* ctx, int64_t n, int64_t m,
                           const int32_t* src, const int32_t* dst,
                           const float* w, uint32_t flags, fj_graph** out);
+
+/* Gives existing edges new weights (the FJ model on a changed graph,
+ * Sec. 3.1), in place: no re-sort, no new layout.  Update i sets the weight
+ * of the pair {src[i], dst[i]} (ids of g, in either orientation) to w[i];
+ * a pair listed several times at upload (FJ_MERGE_DUPLICATES) has its first
+ * listing changed.  The Jacobi preconditioner is recomputed as the upload
+ * computes it, so the graph is the same bits as a fresh upload of the
+ * changed edge list (in the same order).  A graph uploaded without weights
+ * gets a weight array (all ones) first.  A pair should appear at most once
+ * per call (otherwise which of its weights is kept is unspecified).  Warm
+ * starts (fj_solve_warm from the previous z) then re-solve cheaply.
+ *   count      number of updates (>= 0)
+ *   src, dst   int32[count] endpoints; w: float32[count] new weights > 0
+ *   flags      FJ_HOST_PTRS or FJ_DEVICE_PTRS for src, dst, w
+ * Errors: FJ_ERR_ARG, FJ_ERR_GRAPH (an id out of range, a self-loop, a
+ * weight not finite and > 0, or a pair that is not an edge; the graph is
+ * unchanged), FJ_ERR_OOM, FJ_ERR_CUDA. */
+fj_status fj_graph_update_weights(fj_ctx* ctx, fj_graph* g, int64_t count,
+                                  const int32_t* src, const int32_t* dst,
+                                  const float* w, uint32_t flags);
 
 /* Frees a graph made by fj_graph_upload on this context. */
 fj_status fj_graph_free(fj_ctx* ctx, fj_graph* g);
@@ -281,14 +307,87 @@ typedef struct fj_tune_result {
 fj_status fj_tune(fj_ctx* ctx, const fj_graph* g, int32_t k, const double* s,
                   const fj_opts* opts, int32_t repeats, fj_tune_result* out);
 
+/* Many independent problems, each its own graph and opinion vectors, in
+ * shared persistent launches: every problem is cut into parts of 32/16/8/4/
+ * 2/1 columns as in fj_solve_ex, and parts of equal width are packed, up to
+ * FJ_PACK_MAX per launch and up to the blocks the device holds at once, into
+ * one cooperative launch.  Each part runs on its own block range (sized by
+ * its work as fj_solve_ex sizes a grid) with its own grid barrier, reduction
+ * slots, workspace and stopping test, so its results are the same bits as
+ * fj_solve_ex gives for that part on that many blocks (fj_set_grid); small
+ * graphs no longer pay a whole-device launch each.  Launches run one after
+ * another on the context's stream.
+ *   count   number of problems, 1 <= count <= FJ_BATCH_MAX
+ *   graphs  const fj_graph*[count] of this context's device (may repeat)
+ *   k       int32[count], 1 <= k[i] <= 1024
+ *   s       const double*[count]; s[i]: float64[n_i * k_i] column-major,
+ *           host or device per opts->flags
+ *   z       double*[count] or NULL, entries NULL or outputs shaped like s[i]
+ *   quant   fj_quant*[count] or NULL, entries NULL or HOST fj_quant[k_i]
+ *   opts    options shared by all problems (NULL: defaults); FJ_TWO_SOLVES
+ *           is rejected
+ *   info    fj_info[count] or NULL: per problem; blocks = its largest part's
+ *           block range, device_ms = the whole call's device time
+ * Returns FJ_OK, FJ_ERR_ARG / FJ_ERR_OOM / FJ_ERR_CUDA for the call, or the
+ * first problem's solve error (each problem's own in info[i].status). */
+#define FJ_PACK_MAX 24
+#define FJ_BATCH_MAX 4096
+fj_status fj_solve_batch(fj_ctx* ctx, int32_t count,
+                         const fj_graph* const* graphs, const int32_t* k,
+                         const double* const* s, double* const* z,
+                         fj_quant* const* quant, const fj_opts* opts,
+                         fj_info* info);
+
+/* Layout of a graph on the device (the SpMV's row split): rows of more than
+ * sell_max entries are "long" and cut into chunks of at most chunk_len
+ * entries, each walked by a whole warp; shorter rows are stored as sliced
+ * ELL (32-row slices, one lane per row).  The defaults (512, 64) suit the
+ * power-law graphs measured here; fj_tune_layout picks per workload. */
+typedef struct fj_layout {
+  int32_t chunk_len; /* 32 .. 65536 entries (default 512)                    */
+  int32_t sell_max;  /* 8 .. 64 entries (default 64)                         */
+} fj_layout;
+
+/* Later uploads on this context use this layout (NULL: the defaults).
+ * Errors: FJ_ERR_ARG (NULL ctx, values out of range). */
+fj_status fj_set_layout(fj_ctx* ctx, const fj_layout* layout);
+
+/* The layout a graph was built with. */
+fj_status fj_graph_layout(const fj_graph* g, fj_layout* out);
+
+/* Layout autotuner: uploads the edge list (as fj_graph_upload, with
+ * upload_flags) once per candidate layout - chunk lengths 256 to 4096 and
+ * sliced-ELL limits 32 and 64, the default first - and times solves of the k
+ * columns of s on each (solve kernels only, median of `repeats` after one
+ * warm-up).  The fastest becomes the context's layout for later uploads
+ * (fj_set_layout); out lists every candidate and its time.  The layout
+ * changes only the order of floating-point sums, so results stay within the
+ * solve's tolerance.  Errors: FJ_ERR_ARG, and any error of the uploads and
+ * solves it runs. */
+#define FJ_LAYOUT_TUNE_MAX 16
+typedef struct fj_layout_tune_result {
+  fj_layout best;
+  int32_t count;                          /* candidates timed              */
+  fj_layout tried[FJ_LAYOUT_TUNE_MAX];
+  double ms[FJ_LAYOUT_TUNE_MAX];          /* median device milliseconds    */
+} fj_layout_tune_result;
+fj_status fj_tune_layout(fj_ctx* ctx, int64_t n, int64_t m, const int32_t* src,
+                         const int32_t* dst, const float* w,
+                         uint32_t upload_flags, int32_t k, const double* s,
+                         const fj_opts* opts, int32_t repeats,
+                         fj_layout_tune_result* out);
+
 /* ---------------------------------------------------------------------
  * Serving: continuous batching of solve requests (one worker thread per
  * context, started by the first call below).  A request is queued on submit;
  * it is admitted as soon as an in-flight slot is free and the device memory
- * it needs fits the serving budget, and then runs on its own stream, side
- * by side with the other admitted requests.  Finished requests release their
- * memory and slot at once, so queued requests start while others still run.
- * These calls may come from several threads.
+ * it needs fits the serving budget, and then runs side by side with the
+ * other admitted requests (small ones packed together, see fj_serve_pack).
+ * Admission follows arrival order, except that a request that does not fit
+ * the budget yet is passed over by later requests that do, at most 32 times;
+ * after that nothing behind it is admitted until it fits.  Finished requests
+ * release their memory and slot at once, so queued requests start while
+ * others still run.  These calls may come from several threads.
  */
 
 /* Sets the serving limits: at most max_inflight requests on the GPU at once
@@ -302,6 +401,16 @@ fj_status fj_tune(fj_ctx* ctx, const fj_graph* g, int32_t k, const double* s,
 fj_status fj_serve_config(fj_ctx* ctx, int32_t max_inflight,
                           int64_t mem_budget_bytes,
                           int32_t max_blocks_per_request);
+
+/* Requests whose graph has at most max_nodes nodes (default 131072; 0:
+ * none) are solved in packed batches: once their graphs are resident, the
+ * waiting small requests are solved together, their parts of equal column
+ * count packed into shared persistent launches as in fj_solve_batch, each
+ * part on its own block range of at most the per-request block cap.  Larger
+ * requests run their own persistent solve.  A request's results depend only
+ * on its own size and the cap, so they are the same bits packed or not.
+ * Errors: FJ_ERR_ARG, FJ_ERR_CUDA. */
+fj_status fj_serve_pack(fj_ctx* ctx, int64_t max_nodes);
 
 /* Queues the solve of k opinion vectors on a resident graph (which must stay
  * alive until the request is collected).  s: HOST float64[n*k], column-major,

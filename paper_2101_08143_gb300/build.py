@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfj.so")
-SOURCES = ["fj_graph.cu", "fj_solve.cu", "fj_lcc.cu", "fj_api.cpp", "fj_serve.cpp"]
+SOURCES = ["fj_graph.cu", "fj_solve.cu", "fj_lcc.cu", "fj_api.cpp", "fj_serve.cpp", "fj_batch.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
           "-I" + os.path.join(os.path.dirname(HERE), "include")]

@@ -22,9 +22,11 @@
 fj_status fj_lcc_device(const fj_graph* g, cudaStream_t st, fj_graph** out);
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m,
                                 const int32_t* src, const int32_t* dst, const float* w,
-                                bool merge_duplicates, fj_graph** out, int32_t* copy_src = nullptr, int32_t* copy_dst = nullptr,
-                                float* copy_w = nullptr);
+                                bool merge_duplicates, const fj::Layout& lay, fj_graph** out,
+                                int32_t* copy_src = nullptr, int32_t* copy_dst = nullptr, float* copy_w = nullptr);
 fj_status fj_free_graph_device(fj_graph* g, cudaStream_t st);
+fj_status fj_update_weights_device(fj_graph* g, cudaStream_t st, int64_t count, const int32_t* src,
+                                   const int32_t* dst, const float* w);
 size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms);
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k,
                           const double* s, double* z, double* quant, double* resid, int* status,
@@ -37,6 +39,7 @@ struct Request;
 Server* server_create(int device, int num_sms);
 void server_destroy(Server* S);
 fj_status server_config(Server* S, int32_t max_inflight, int64_t budget, int32_t max_blocks);
+fj_status server_pack(Server* S, int64_t max_nodes);
 fj_status server_submit(Server* S, Request* r, uint64_t* ticket);
 fj_status server_poll(Server* S, uint64_t ticket, int32_t timeout_us, fj_quant* out, fj_info* info);
 Request* request_new();
@@ -123,6 +126,7 @@ struct fj_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int max_blocks = 0;  // 0: all co-resident blocks
   int grid = 0;        // > 0: exactly this many blocks (fj_set_grid)
+  fj::Layout layout;   // layout of later uploads (fj_set_layout)
   std::mutex server_mu;
   fj::Server* server = nullptr;  // created by the first fj_submit / fj_serve_config
 };
@@ -220,6 +224,31 @@ fj_status status_from_bits(int bits) {
 }
 
 }  // namespace
+
+// Context internals for fj_batch.cpp: the device, its SM count and the
+// context's stream; and grow-only device scratch (0: solver workspace, 1:
+// small outputs, 2: staged s, 3: staged z).
+fj_status fj::ctx_device(fj_ctx* c, int* device, int* num_sms, cudaStream_t* st) {
+  *device = c->device;
+  *num_sms = c->num_sms;
+  *st = c->stream;
+  return FJ_OK;
+}
+
+fj_status fj::ctx_scratch(fj_ctx* c, int which, size_t bytes, char** out) {
+  void** p = nullptr;
+  size_t* have = nullptr;
+  switch (which) {
+    case 0: p = (void**)&c->ws; have = &c->ws_bytes; break;
+    case 1: p = (void**)&c->small; have = &c->small_bytes; break;
+    case 2: p = (void**)&c->s_dev; have = &c->s_bytes; break;
+    default: p = (void**)&c->z_dev; have = &c->z_bytes; break;
+  }
+  fj_status rc = grow(p, have, bytes);
+  if (rc != FJ_OK) return rc;
+  *out = (char*)*p;
+  return FJ_OK;
+}
 
 extern "C" {
 
@@ -339,7 +368,7 @@ fj_status fj_graph_upload(fj_ctx* c, int64_t n, int64_t m, const int32_t* src, c
   FJ_CUDA(cudaSetDevice(c->device));
   const bool merge = (flags & FJ_MERGE_DUPLICATES) != 0;
   if (flags & FJ_DEVICE_PTRS)
-    return fj_build_graph_device(c->device, c->stream, n, m, src, dst, w, merge, out);
+    return fj_build_graph_device(c->device, c->stream, n, m, src, dst, w, merge, c->layout, out);
   // host edge list: copy it to the device first
   int32_t *ds = nullptr, *dd = nullptr;
   float* dw = nullptr;
@@ -362,7 +391,7 @@ fj_status fj_graph_upload(fj_ctx* c, int64_t n, int64_t m, const int32_t* src, c
   const void* mw = w ? mapped_host(w) : nullptr;
   if (m > 0 && ms && md && (!w || mw)) {
     rc = fj_build_graph_device(c->device, c->stream, n, m, (const int32_t*)ms, (const int32_t*)md,
-                               (const float*)mw, merge, out, ds, dd, dw);
+                               (const float*)mw, merge, c->layout, out, ds, dd, dw);
   } else {
     if (m > 0) {
       cudaError_t e = cudaMemcpyAsync(ds, src, m * 4, cudaMemcpyHostToDevice, c->stream);
@@ -370,7 +399,8 @@ fj_status fj_graph_upload(fj_ctx* c, int64_t n, int64_t m, const int32_t* src, c
       if (e == cudaSuccess && w) e = cudaMemcpyAsync(dw, w, m * 4, cudaMemcpyHostToDevice, c->stream);
       if (e != cudaSuccess) rc = cuda_fail(e, "fj_graph_upload copy");
     }
-    if (rc == FJ_OK) rc = fj_build_graph_device(c->device, c->stream, n, m, ds, dd, w ? dw : nullptr, merge, out);
+    if (rc == FJ_OK)
+      rc = fj_build_graph_device(c->device, c->stream, n, m, ds, dd, w ? dw : nullptr, merge, c->layout, out);
   }
   cudaFreeAsync(ds, c->stream);
   cudaFreeAsync(dd, c->stream);
@@ -388,6 +418,73 @@ fj_status fj_graph_free(fj_ctx* c, fj_graph* g) {
   forget_tuned_grids(g);
   FJ_CUDA(cudaSetDevice(c->device));
   return fj_free_graph_device(g, c->stream);
+}
+
+fj_status fj_set_layout(fj_ctx* c, const fj_layout* l) {
+  if (!c) {
+    set_error("fj_set_layout: ctx is NULL");
+    return FJ_ERR_ARG;
+  }
+  fj::Layout lay;
+  if (l) {
+    if (l->chunk_len < 32 || l->chunk_len > 65536 || l->sell_max < 8 || l->sell_max > kSellMaxLenLimit) {
+      set_error("fj_set_layout: need 32 <= chunk_len <= 65536 and 8 <= sell_max <= %d", kSellMaxLenLimit);
+      return FJ_ERR_ARG;
+    }
+    lay.chunk_len = l->chunk_len;
+    lay.sell_max = l->sell_max;
+  }
+  c->layout = lay;
+  return FJ_OK;
+}
+
+fj_status fj_graph_layout(const fj_graph* g, fj_layout* out) {
+  if (!g || !out) {
+    set_error("fj_graph_layout: graph and out must be non-NULL");
+    return FJ_ERR_ARG;
+  }
+  out->chunk_len = g->chunk_len;
+  out->sell_max = g->sell_max;
+  return FJ_OK;
+}
+
+fj_status fj_graph_update_weights(fj_ctx* c, fj_graph* g, int64_t count, const int32_t* src, const int32_t* dst,
+                                  const float* w, uint32_t flags) {
+  if (!c || !g || count < 0 || (count > 0 && (!src || !dst || !w)) || (flags & ~FJ_DEVICE_PTRS)) {
+    set_error("fj_graph_update_weights: ctx and graph must be non-NULL, count >= 0, src/dst/w non-NULL");
+    return FJ_ERR_ARG;
+  }
+  if (g->device != c->device) {
+    set_error("fj_graph_update_weights: graph belongs to device %d, context to %d", g->device, c->device);
+    return FJ_ERR_ARG;
+  }
+  if (count == 0) return FJ_OK;
+  FJ_CUDA(cudaSetDevice(c->device));
+  if (flags & FJ_DEVICE_PTRS) return fj_update_weights_device(g, c->stream, count, src, dst, w);
+  int32_t *ds = nullptr, *dd = nullptr;
+  float* dw = nullptr;
+  if (malloc_async(&ds, (size_t)count * 4, c->stream) != cudaSuccess ||
+      malloc_async(&dd, (size_t)count * 4, c->stream) != cudaSuccess ||
+      malloc_async(&dw, (size_t)count * 4, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    if (ds) cudaFreeAsync(ds, c->stream);
+    if (dd) cudaFreeAsync(dd, c->stream);
+    set_error("fj_graph_update_weights: out of device memory");
+    return FJ_ERR_OOM;
+  }
+  fj_status rc = FJ_OK;
+  cudaError_t e = cudaMemcpyAsync(ds, src, (size_t)count * 4, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dd, dst, (size_t)count * 4, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dw, w, (size_t)count * 4, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess)
+    rc = cuda_fail(e, "fj_graph_update_weights copy");
+  else
+    rc = fj_update_weights_device(g, c->stream, count, ds, dd, dw);
+  cudaFreeAsync(ds, c->stream);
+  cudaFreeAsync(dd, c->stream);
+  cudaFreeAsync(dw, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return rc;
 }
 
 fj_status fj_graph_lcc(fj_ctx* c, const fj_graph* g, fj_graph** out) {
@@ -632,6 +729,63 @@ fj_status fj_tune(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, cons
   return FJ_OK;
 }
 
+fj_status fj_tune_layout(fj_ctx* c, int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const float* w,
+                         uint32_t upload_flags, int32_t k, const double* s, const fj_opts* opts, int32_t repeats,
+                         fj_layout_tune_result* out) {
+  if (!c || !s || !out || k < 1 || repeats < 1 || repeats > 64) {
+    set_error("fj_tune_layout: ctx, s and out must be non-NULL, k >= 1, 1 <= repeats <= 64");
+    return FJ_ERR_ARG;
+  }
+  memset(out, 0, sizeof(*out));
+  fj_opts o;
+  fj_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.flags & FJ_TWO_SOLVES) {
+    set_error("fj_tune_layout: FJ_TWO_SOLVES is not tuned");
+    return FJ_ERR_ARG;
+  }
+  // candidates: chunk lengths 256..4096 entries, sliced-ELL rows of up to
+  // 32 or 64 entries; the default (512, 64) first
+  std::vector<fj::Layout> cand;
+  cand.push_back(fj::Layout());
+  for (int sm : {64, 32})
+    for (int cl : {256, 512, 1024, 2048, 4096}) {
+      fj::Layout l;
+      l.chunk_len = cl;
+      l.sell_max = sm;
+      if (!(cl == kChunkLen && sm == kSellMaxLen)) cand.push_back(l);
+    }
+  const fj::Layout saved = c->layout;
+  fj_status rc = FJ_OK;
+  double best_ms = 0.0;
+  for (size_t i = 0; i < cand.size() && i < FJ_LAYOUT_TUNE_MAX && rc == FJ_OK; ++i) {
+    c->layout = cand[i];
+    fj_graph* g = nullptr;
+    rc = fj_graph_upload(c, n, m, src, dst, w, upload_flags, &g);
+    if (rc != FJ_OK) break;
+    std::vector<double> ms;
+    for (int r = 0; r <= repeats && rc == FJ_OK; ++r) {
+      fj_info info;
+      rc = fj_solve_ex(c, g, k, s, nullptr, nullptr, &o, &info);
+      if (r > 0) ms.push_back(info.device_ms);
+    }
+    fj_graph_free(c, g);
+    if (rc != FJ_OK) break;
+    std::sort(ms.begin(), ms.end());
+    out->tried[i].chunk_len = cand[i].chunk_len;
+    out->tried[i].sell_max = cand[i].sell_max;
+    out->ms[i] = ms[ms.size() / 2];
+    out->count = (int32_t)i + 1;
+    if (i == 0 || out->ms[i] < best_ms) {
+      best_ms = out->ms[i];
+      out->best = out->tried[i];
+    }
+  }
+  c->layout = saved;
+  if (rc != FJ_OK) return rc;
+  return fj_set_layout(c, &out->best);
+}
+
 // ------------------------------------------------------------- serving
 
 static fj_status get_server(fj_ctx* c, fj::Server** out) {
@@ -672,6 +826,17 @@ fj_status fj_serve_config(fj_ctx* c, int32_t max_inflight, int64_t mem_budget_by
   fj_status rc = get_server(c, &S);
   if (rc != FJ_OK) return rc;
   return server_config(S, max_inflight, mem_budget_bytes, max_blocks_per_request);
+}
+
+fj_status fj_serve_pack(fj_ctx* c, int64_t max_nodes) {
+  if (!c || max_nodes < 0) {
+    set_error("fj_serve_pack: bad argument");
+    return FJ_ERR_ARG;
+  }
+  fj::Server* S = nullptr;
+  fj_status rc = get_server(c, &S);
+  if (rc != FJ_OK) return rc;
+  return server_pack(S, max_nodes);
 }
 
 fj_status fj_submit(fj_ctx* c, const fj_graph* g, int32_t k, const double* s, const fj_opts* opts,

@@ -412,15 +412,16 @@ __global__ void k_apply_perm(const int32_t* __restrict__ perm, const int32_t* __
   }
 }
 
-// out[0] = n_long, the number of rows with more than kSellMaxLen entries;
+// out[0] = n_long, the number of rows with more than sell_max entries;
 // out[1] = n_nz, the number of rows with at least one entry (in solver order
 // both are prefixes of the rows).
-__global__ void k_count_long(const int32_t* __restrict__ row_ptr, int64_t n, int64_t* __restrict__ out) {
+__global__ void k_count_long(const int32_t* __restrict__ row_ptr, int64_t n, int64_t* __restrict__ out,
+                             int32_t sell_max) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t d = row_ptr[i + 1] - row_ptr[i];
     const int32_t dn = (i + 1 < n) ? row_ptr[i + 2] - row_ptr[i + 1] : 0;
-    if (d > kSellMaxLen && dn <= kSellMaxLen) out[0] = i + 1;
+    if (d > sell_max && dn <= sell_max) out[0] = i + 1;
     if (d > 0 && dn == 0) out[1] = i + 1;
   }
 }
@@ -432,7 +433,7 @@ __global__ void k_count_long(const int32_t* __restrict__ row_ptr, int64_t n, int
 // entries past the live counts are 0 so that scans over upper bounds work.
 __global__ void k_layout_sizes(const int32_t* __restrict__ row_ptr, int64_t n, int64_t* __restrict__ cnt,
                                int64_t ns_cap, int64_t nl_cap, int64_t* __restrict__ slice_off,
-                               int32_t* __restrict__ long_first) {
+                               int32_t* __restrict__ long_first, int32_t chunk_len) {
   const int64_t n_long = cnt[0];
   const int64_t n_nz = cnt[1] > n_long ? cnt[1] : n_long;
   const int64_t n_slices = (n_nz - n_long + 31) / 32;
@@ -446,7 +447,7 @@ __global__ void k_layout_sizes(const int32_t* __restrict__ row_ptr, int64_t n, i
       slice_off[i] = (i < n_slices) ? 32 * (int64_t)(row_ptr[n_long + 32 * i + 1] - row_ptr[n_long + 32 * i]) : 0;
     } else {
       const int64_t r = i - ns_cap - 1;  // r in [0, nl_cap]
-      long_first[r] = (r < n_long) ? (row_ptr[r + 1] - row_ptr[r] + kChunkLen - 1) / kChunkLen : 0;
+      long_first[r] = (r < n_long) ? (row_ptr[r + 1] - row_ptr[r] + chunk_len - 1) / chunk_len : 0;
     }
   }
 }
@@ -467,7 +468,7 @@ constexpr int64_t kCostSlice = 8 * 1055, kCostSliceStep = 8 * 250;
 __global__ void k_units(const int32_t* __restrict__ row_ptr, int64_t* __restrict__ cnt,
                         const int32_t* __restrict__ long_first, const int64_t* __restrict__ slice_off,
                         int64_t units_cap, int32_t* __restrict__ chunk_row, int32_t* __restrict__ chunk_begin,
-                        int32_t* __restrict__ chunk_end, int64_t* __restrict__ unit_cost) {
+                        int32_t* __restrict__ chunk_end, int64_t* __restrict__ unit_cost, int32_t chunk_len) {
   const int64_t n_long = cnt[0], n_slices = cnt[2];
   const int64_t n_chunks = long_first[n_long];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -478,8 +479,8 @@ __global__ void k_units(const int32_t* __restrict__ row_ptr, int64_t* __restrict
        r += (int64_t)gridDim.x * blockDim.x) {
     const int32_t b = row_ptr[r], e = row_ptr[r + 1];
     for (int32_t c = long_first[r], q = 0; c < long_first[r + 1]; ++c, ++q) {
-      const int32_t cb = b + q * kChunkLen;
-      const int32_t ce = cb + kChunkLen < e ? cb + kChunkLen : e;
+      const int32_t cb = b + q * chunk_len;
+      const int32_t ce = cb + chunk_len < e ? cb + chunk_len : e;
       chunk_row[c] = (int32_t)r;
       chunk_begin[c] = cb;
       chunk_end[c] = ce;
@@ -805,8 +806,9 @@ constexpr int kBuildWords = 9;
 // that copy has completed; host_words must stay valid until then (page-locked
 // memory for an asynchronous copy).
 fj_status fj_build_graph_begin(int device, cudaStream_t st, int64_t n, int64_t m, const int32_t* src,
-                               const int32_t* dst, const float* w, bool merge_duplicates, int64_t* host_words,
-                               fj_graph** pending, int32_t* copy_src, int32_t* copy_dst, float* copy_w) {
+                               const int32_t* dst, const float* w, bool merge_duplicates, const Layout& lay,
+                               int64_t* host_words, fj_graph** pending, int32_t* copy_src, int32_t* copy_dst,
+                               float* copy_w) {
   fj_graph** out = pending;
   const int64_t N = 2 * m;
   const bool weighted = (w != nullptr);
@@ -855,6 +857,8 @@ fj_status fj_build_graph_begin(int device, cudaStream_t st, int64_t n, int64_t m
   g->device = device;
   g->n = n;
   g->weighted = weighted ? 1 : 0;
+  g->chunk_len = lay.chunk_len;
+  g->sell_max = lay.sell_max;
   auto fail = [&](fj_status code) {
     fj_free_graph_arrays(g, st);
     delete g;
@@ -878,12 +882,12 @@ fj_status fj_build_graph_begin(int device, cudaStream_t st, int64_t n, int64_t m
   // the degrees alone.  Sizes stay on the device; buffers use upper bounds:
   // in decreasing-degree order a slice's first row is no longer than any row
   // of the slice before it, so the sliced ELL holds at most
-  // nnz + 32 * kSellMaxLen entries.
-  const int64_t nl_cap = std::min<int64_t>(n, N / (kSellMaxLen + 1));
+  // nnz + 32 * sell_max entries.
+  const int64_t nl_cap = std::min<int64_t>(n, N / (lay.sell_max + 1));
   const int64_t ns_cap = (n + 31) / 32;
-  const int64_t nc_cap = nl_cap + N / kChunkLen + 1;
+  const int64_t nc_cap = nl_cap + N / lay.chunk_len + 1;
   const int64_t units_cap = nc_cap + ns_cap;
-  const int64_t sell_cap = N + 32 * kSellMaxLen;
+  const int64_t sell_cap = N + 32 * (int64_t)lay.sell_max;
   if (malloc_async(&g->col, (N + kPad) * 4, st) != cudaSuccess ||
       (weighted && malloc_async(&g->val, (N + kPad) * 4, st) != cudaSuccess) ||
       malloc_async(&g->slice_off, (ns_cap + 1) * 8, st) != cudaSuccess ||
@@ -901,16 +905,16 @@ fj_status fj_build_graph_begin(int device, cudaStream_t st, int64_t n, int64_t m
   cudaMemsetAsync(g->col + N, 0, kPad * 4, st);
   if (weighted) cudaMemsetAsync(g->val + N, 0, kPad * 4, st);
   count_launches(2);
-  k_count_long<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, dcnt);
+  k_count_long<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, dcnt, lay.sell_max);
   k_layout_sizes<<<grid_for(ns_cap + nl_cap + 2, 256), 256, 0, st>>>(g->row_ptr, n, dcnt, ns_cap, nl_cap,
-                                                                    g->slice_off, g->long_first);
+                                                                    g->slice_off, g->long_first, lay.chunk_len);
   rc = exclusive_scan<int64_t>(g->slice_off, ns_cap + 1, st);
   if (rc == FJ_OK) rc = exclusive_scan<int32_t>(g->long_first, nl_cap + 1, st);
   if (rc != FJ_OK) return fail(rc);
   count_launches(2);
   k_units<<<grid_for(std::max(nl_cap, units_cap + 1), 256), 256, 0, st>>>(
       g->row_ptr, dcnt, g->long_first, g->slice_off, units_cap, g->chunk_row, g->chunk_begin, g->chunk_end,
-      g->unit_prefix);
+      g->unit_prefix, lay.chunk_len);
   k_sell_pad<<<grid_for(ns_cap * 32, 256), 256, 0, st>>>(g->row_ptr, n, dcnt, g->slice_off, g->sell_col,
                                                          g->sell_val);
   if (cudaGetLastError() != cudaSuccess) return fail(FJ_ERR_CUDA);
@@ -1020,13 +1024,13 @@ fj_status fj_build_graph_end(fj_graph* g, const int64_t* hc, cudaStream_t st, fj
 
 // Both halves with the host waiting in between.
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m, const int32_t* src,
-                                const int32_t* dst, const float* w, bool merge_duplicates, fj_graph** out,
-                                int32_t* copy_src, int32_t* copy_dst, float* copy_w) {
+                                const int32_t* dst, const float* w, bool merge_duplicates, const Layout& lay,
+                                fj_graph** out, int32_t* copy_src, int32_t* copy_dst, float* copy_w) {
   int64_t hc[kBuildWords];
   fj_graph* g = nullptr;
   *out = nullptr;
-  fj_status rc = fj_build_graph_begin(device, st, n, m, src, dst, w, merge_duplicates, hc, &g, copy_src, copy_dst,
-                                      copy_w);
+  fj_status rc = fj_build_graph_begin(device, st, n, m, src, dst, w, merge_duplicates, lay, hc, &g, copy_src,
+                                      copy_dst, copy_w);
   if (rc != FJ_OK) return rc;
   const cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -1042,5 +1046,168 @@ fj_status fj_free_graph_device(fj_graph* g, cudaStream_t st) {
   fj_free_graph_arrays(g, st);
   FJ_CUDA(cudaStreamSynchronize(st));
   delete g;
+  return FJ_OK;
+}
+
+// ------------------------------------------------------- weight updates
+//
+// New weights for existing edges of a resident graph (the FJ model on a
+// changed graph, Sec. 3.1): the entries of each updated pair are found in
+// both of its rows and rewritten in the CSR and the sliced ELL, then the
+// Jacobi preconditioner is recomputed by the kernels and summation order of
+// the build.  A pair listed several times (FJ_MERGE_DUPLICATES) has several
+// entries per row; the update rewrites the first, which belongs to the
+// first listing of the pair.
+
+namespace fj {
+
+__global__ void k_inverse_perm(const int32_t* __restrict__ perm, int64_t n, int32_t* __restrict__ inv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    inv[perm[i]] = (int32_t)i;
+}
+
+// Sliced-ELL weights of a graph built without weights: 1 for entries, 0 for
+// the padding (as the build writes them).
+__global__ void k_sell_unit_vals(const int32_t* __restrict__ row_ptr, int64_t n, int64_t n_long, int64_t n_slices,
+                                 const int64_t* __restrict__ slice_off, float* __restrict__ sell_val) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; s < n_slices;
+       s += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t row = n_long + 32 * s + lane;
+    const int32_t len = row < n ? row_ptr[row + 1] - row_ptr[row] : 0;
+    const int64_t off = slice_off[s];
+    const int32_t slen = (int32_t)((slice_off[s + 1] - off) >> 5);
+    for (int32_t p = 0; p < slen; ++p) sell_val[off + 32 * (int64_t)p + lane] = p < len ? 1.0f : 0.0f;
+  }
+}
+
+__global__ void k_fill_f32(float* __restrict__ a, int64_t count, float v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+// One warp per update u: pair (src[u], dst[u]) in input ids gets weight
+// w[u].  With apply == false it only checks (ids, weight, that the pair is
+// an edge) and records the first bad update in err ([0] bits, [1] index);
+// with apply == true it writes both directed entries.
+__global__ void k_update_weights(int64_t count, int64_t n, const int32_t* __restrict__ src,
+                                 const int32_t* __restrict__ dst, const float* __restrict__ w,
+                                 const int32_t* __restrict__ inv, const int32_t* __restrict__ row_ptr,
+                                 const int32_t* __restrict__ col, float* __restrict__ val, int64_t n_long,
+                                 const int64_t* __restrict__ slice_off, float* __restrict__ sell_val, bool apply,
+                                 unsigned long long* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < count;
+       u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t a = src[u], b = dst[u];
+    const float wn = w[u];
+    unsigned long long bad = 0;
+    if (a < 0 || b < 0 || a >= n || b >= n || a == b) bad = kErrBadId;
+    else if (!(wn > 0.0f) || !isfinite(wn)) bad = kErrBadWeight;
+    for (int dir = 0; dir < 2 && !bad; ++dir) {
+      const int32_t r = inv[dir ? b : a], c = inv[dir ? a : b];
+      const int32_t e = row_ptr[r + 1];
+      int32_t first = -1;
+      for (int32_t base = row_ptr[r]; base < e; base += 32) {
+        const int32_t p = base + lane;
+        const unsigned hit = __ballot_sync(kFull, p < e && col[p] == c);
+        if (hit) {
+          first = base + __ffs(hit) - 1;
+          break;
+        }
+      }
+      if (first < 0) {
+        bad = kErrDuplicate;  // (reused bit) the pair is not an edge
+      } else if (apply && lane == 0) {
+        val[first] = wn;
+        if (r >= n_long) {
+          const int64_t sr = r - n_long;
+          sell_val[slice_off[sr >> 5] + 32 * (int64_t)(first - row_ptr[r]) + (sr & 31)] = wn;
+        }
+      }
+    }
+    if (bad && lane == 0) {
+      atomicOr(&err[0], bad);
+      atomicMin(&err[1], (unsigned long long)u);
+    }
+  }
+}
+
+}  // namespace fj
+
+// Called by the C ABI (fj_api.cpp): src/dst/w are device pointers of count
+// updates.  On FJ_ERR_GRAPH nothing was changed.
+fj_status fj_update_weights_device(fj_graph* g, cudaStream_t st, int64_t count, const int32_t* src,
+                                   const int32_t* dst, const float* w) {
+  if (count == 0) return FJ_OK;
+  const int64_t n = g->n, N = g->nnz;
+  Pool pool(st);
+  int32_t* inv = pool.get<int32_t>(n);
+  unsigned long long* err = pool.get<unsigned long long>(2);
+  int64_t* dcnt = pool.get<int64_t>(2);
+  if (!inv || !err || !dcnt) {
+    set_error("fj_graph_update_weights: out of device memory");
+    return FJ_ERR_OOM;
+  }
+  const unsigned long long init[2] = {0ull, ~0ull};
+  FJ_CUDA(cudaMemcpyAsync(err, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  count_launches(2);
+  k_inverse_perm<<<grid_for(n, 256), 256, 0, st>>>(g->perm, n, inv);
+  k_update_weights<<<grid_for(count * 32, 256), 256, 0, st>>>(count, n, src, dst, w, inv, g->row_ptr, g->col,
+                                                               g->val, g->n_long, g->slice_off, g->sell_val,
+                                                               false, err);
+  FJ_CUDA(cudaGetLastError());
+  unsigned long long herr[2];
+  FJ_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st));
+  FJ_CUDA(cudaStreamSynchronize(st));
+  if (herr[0]) {
+    set_error("fj_graph_update_weights: update %llu %s", herr[1],
+              (herr[0] & kErrBadId)       ? "has a node id outside [0, n) or a self-loop"
+              : (herr[0] & kErrBadWeight) ? "has a weight that is not finite and > 0"
+                                          : "names a pair that is not an edge of the graph");
+    return FJ_ERR_GRAPH;
+  }
+  if (!g->weighted) {
+    // a graph built without weights gets its weight arrays (all ones)
+    const int64_t sell_cap = N + 32 * (int64_t)g->sell_max;
+    float* val = nullptr;
+    float* sell_val = nullptr;
+    if (malloc_async(&val, (N + kPad) * 4, st) != cudaSuccess ||
+        malloc_async(&sell_val, (sell_cap + kPad) * 4, st) != cudaSuccess) {
+      cudaGetLastError();
+      if (val) cudaFreeAsync(val, st);
+      set_error("fj_graph_update_weights: out of device memory for the weights");
+      return FJ_ERR_OOM;
+    }
+    count_launches(3);
+    k_fill_f32<<<grid_for(N, 256), 256, 0, st>>>(val, N, 1.0f);
+    FJ_CUDA(cudaMemsetAsync(val + N, 0, kPad * 4, st));
+    k_fill_f32<<<grid_for(sell_cap + kPad, 256), 256, 0, st>>>(sell_val, sell_cap + kPad, 0.0f);
+    k_sell_unit_vals<<<grid_for(g->n_slices * 32, 256), 256, 0, st>>>(g->row_ptr, n, g->n_long, g->n_slices,
+                                                                      g->slice_off, sell_val);
+    FJ_CUDA(cudaGetLastError());
+    g->val = val;
+    g->sell_val = sell_val;
+    g->weighted = 1;
+  }
+  count_launches(1);
+  k_update_weights<<<grid_for(count * 32, 256), 256, 0, st>>>(count, n, src, dst, w, inv, g->row_ptr, g->col,
+                                                               g->val, g->n_long, g->slice_off, g->sell_val,
+                                                               true, err);
+  // the preconditioner, as the build computes it
+  const int64_t hc[2] = {g->n_long, g->n_nz};
+  FJ_CUDA(cudaMemcpyAsync(dcnt, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+  float* cpart = pool.get<float>(std::max<int64_t>(g->n_chunks, 1));
+  if (!cpart) {
+    set_error("fj_graph_update_weights: out of device memory");
+    return FJ_ERR_OOM;
+  }
+  count_launches(2);
+  k_chunk_wsum<<<grid_for(std::max<int64_t>(g->n_chunks, 1) * 32, 256), 256, 0, st>>>(
+      g->val, g->long_first, dcnt, g->chunk_begin, g->chunk_end, cpart);
+  k_dinv_weighted<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, dcnt, g->long_first, cpart, g->slice_off,
+                                                    g->sell_val, g->dinv);
+  FJ_CUDA(cudaGetLastError());
+  FJ_CUDA(cudaStreamSynchronize(st));
   return FJ_OK;
 }

@@ -28,10 +28,18 @@ namespace fj {
 // Extra elements after the sort buffers and col/val (batched loads past the
 // last entry stay inside the allocation).
 constexpr int kPad = 64;
-// Rows with at most kSellMaxLen entries go to sliced ELL; longer rows are
-// processed warp-wide in chunks of at most kChunkLen entries.
+// Default layout: rows with at most kSellMaxLen entries go to sliced ELL;
+// longer rows are processed warp-wide in chunks of at most kChunkLen
+// entries.  Both are per graph (fj_set_layout, fj_tune_layout); the sliced
+// ELL threshold is at most kSellMaxLenLimit (the repeated-pair check of short
+// rows handles rows of up to 64 entries).
 constexpr int kSellMaxLen = 64;
 constexpr int kChunkLen = 512;
+constexpr int kSellMaxLenLimit = 64;
+struct Layout {
+  int32_t chunk_len = kChunkLen;
+  int32_t sell_max = kSellMaxLen;
+};
 // Degree keys of the reordering sort saturate here (8-bit keys: one radix
 // pass).  Rows of more than kSellMaxLen entries come first either way, and
 // shorter rows are fully ordered by length; rows of degree >= kDegKeyMax
@@ -85,6 +93,9 @@ struct fj_graph {
   // work units: chunks, then slices
   int64_t n_units;
   int64_t* unit_prefix;  // [n_units + 1]
+  // layout parameters the graph was built with
+  int32_t chunk_len;
+  int32_t sell_max;
 };
 
 namespace fj {
@@ -162,6 +173,23 @@ __device__ __forceinline__ void st_cs(float2* a, float2 v) {
 // ------------------------------------------------------------------- host
 
 namespace fj {
+// One problem of a packed solve launch (several small problems of the same
+// column count K in one cooperative launch): K columns of opinions on a
+// graph, all device pointers.
+struct PackItem {
+  const fj_graph* g;
+  const double* s;  // column 0 of the K columns; column c at s + c * ld
+  int64_t ld;
+  double* z;        // same layout as s, or null
+  double* quant;    // [K][5]
+  double* resid;    // [K]
+  int* status;      // [3]: error bits, iterations, refinements
+  char* ws;         // workspace of fj_solve_workspace_bytes(g, K, ...)
+  size_t ws_bytes;
+  int blocks;       // blocks of the problem's share of the launch
+  fj_opts opts;     // the problem's tolerances and caps (the launch's
+                    // precision is the same for all its problems)
+};
 // Stream-ordered allocation from the library's memory pool of the current
 // device.  The pool keeps freed memory for reuse (its release threshold is
 // unlimited), so repeated uploads and solves do not map and unmap pages.
@@ -176,6 +204,9 @@ void set_error(const char* fmt, ...);
 // Counts kernel launches made by the library (all contexts, this process).
 void count_launches(int k);
 fj_status cuda_fail(cudaError_t e, const char* what);
+// Context internals shared by the C-ABI files (defined in fj_api.cpp).
+fj_status ctx_device(fj_ctx* c, int* device, int* num_sms, cudaStream_t* st);
+fj_status ctx_scratch(fj_ctx* c, int which, size_t bytes, char** out);
 }  // namespace fj
 
 #define FJ_CUDA(call)                                           \

@@ -20,7 +20,8 @@
 #include "fj_internal.cuh"
 
 fj_status fj_build_graph_device(int device, cudaStream_t st, int64_t n, int64_t m, const int32_t* src,
-                                const int32_t* dst, const float* w, bool merge_duplicates, fj_graph** out, int32_t* copy_src = nullptr, int32_t* copy_dst = nullptr,
+                                const int32_t* dst, const float* w, bool merge_duplicates, const fj::Layout& lay,
+                                fj_graph** out, int32_t* copy_src = nullptr, int32_t* copy_dst = nullptr,
                                 float* copy_w = nullptr);
 
 namespace fj {
@@ -384,7 +385,10 @@ fj_status fj_lcc_device(const fj_graph* g, cudaStream_t st, fj_graph** out) {
   // ---- 4. build it like an upload (the pairs are distinct unless g merged
   // repeated pairs, whose parallel entries are kept as such)
   fj_graph* lg = nullptr;
-  rc = fj_build_graph_device(g->device, st, std::max<int64_t>(n_lcc, 1), m_lcc, src, dst, w, true, &lg);
+  fj::Layout lay;
+  lay.chunk_len = g->chunk_len;
+  lay.sell_max = g->sell_max;
+  rc = fj_build_graph_device(g->device, st, std::max<int64_t>(n_lcc, 1), m_lcc, src, dst, w, true, lay, &lg);
   if (rc != FJ_OK) return fail(rc);
   lg->orig_ids = ids;
   cleanup();

@@ -1,18 +1,25 @@
 // fj_serve.cpp - continuous-batching request server behind fj_submit/fj_poll.
 //
 // One worker thread per context owns the device side of serving:
-//   * submitted requests wait in a FIFO queue (inputs already copied);
+//   * submitted requests wait in a queue (inputs already copied);
 //   * a request is admitted when an in-flight slot is free and the device
-//     memory it needs fits the remaining budget; it then runs on the slot's
-//     own stream with its own workspace (graph build for inline requests,
-//     H2D of s, the persistent solve, D2H of the quantities into the slot's
-//     pinned buffer, an event);
-//   * the worker polls the events of in-flight requests and retires them as
-//     they finish, freeing memory and slots so that queued requests start
-//     while others are still running on the GPU.
-// Small requests get small persistent grids, so several run on the GPU at
-// once; a request's grid depends only on its own size and the server's cap,
-// so its results are the same bits alone or in a mix.
+//     memory it needs fits the remaining budget.  Admission goes in arrival
+//     order, but a request that does not fit yet is passed over by later
+//     requests that do, at most kMaxPassOver times; after that nothing behind
+//     it is admitted until it fits, so a large request cannot starve;
+//   * an admitted request builds its own graph (if it brought an edge list)
+//     on its slot's stream; once the graph is resident the request is ready:
+//       - a small graph (at most pack_max_nodes nodes) joins the next batch:
+//         the ready small requests are solved together, their parts of equal
+//         column count packed into shared persistent launches
+//         (fj_solve_packed_device), on one of kBatchStreams batch streams;
+//       - a larger graph runs its own persistent solve on its slot's stream;
+//   * the worker polls the events of builds, solves and batches and retires
+//     requests as they finish, freeing memory and slots at once, so queued
+//     requests start while others are still running on the GPU.
+// A request's grid (or block range in a batch) depends only on its own size
+// and the server's per-request cap, so its results are the same bits alone
+// or in a mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,6 +27,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -29,17 +37,24 @@
 #include "fj_internal.cuh"
 
 fj_status fj_build_graph_begin(int device, cudaStream_t st, int64_t n, int64_t m, const int32_t* src,
-                               const int32_t* dst, const float* w, bool merge_duplicates, int64_t* host_words,
-                               fj_graph** pending, int32_t* copy_src = nullptr, int32_t* copy_dst = nullptr,
-                               float* copy_w = nullptr);
+                               const int32_t* dst, const float* w, bool merge_duplicates, const fj::Layout& lay,
+                               int64_t* host_words, fj_graph** pending, int32_t* copy_src = nullptr,
+                               int32_t* copy_dst = nullptr, float* copy_w = nullptr);
 fj_status fj_build_graph_end(fj_graph* g, const int64_t* host_words, cudaStream_t st, fj_graph** out);
 void fj_free_graph_arrays(fj_graph* g, cudaStream_t st);
 size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms);
+size_t fj_solve_workspace_bytes_blocks(const fj_graph* g, int K, int inner_bytes, int64_t blocks);
 fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32_t k, const double* s, double* z,
                           double* quant, double* resid, int* status, char* ws, size_t ws_bytes, const fj_opts& o,
                           int* launches_out, int max_blocks, const double* z0, int* grid_out);
+fj_status fj_solve_packed_device(int K, int count, const fj::PackItem* items, cudaStream_t st, const fj_opts& o,
+                                 char* bars);
+int fj_pack_blocks(const fj_graph* g, int K, int cap);
+fj_status fj_pack_capacity(int precision, int K, int num_sms, int* out);
 
 namespace fj {
+
+std::vector<std::pair<int, int>> plan_packs(const std::vector<int>& blocks, int capacity);
 
 constexpr int kSlotMaxK = 1024;  // columns per request (pinned result buffers)
 constexpr int kBuildWords = 9;   // a graph build's host words (sizes, validation)
@@ -47,6 +62,11 @@ constexpr int kBuildWords = 9;   // a graph build's host words (sizes, validatio
 // the build words
 constexpr size_t kSlotResultBytes = (size_t)kSlotMaxK * 6 * 8 + 64 * 12;
 constexpr size_t kSlotPinnedBytes = kSlotResultBytes + kBuildWords * 8;
+// later requests admitted ahead of one that does not fit, at most
+constexpr int kMaxPassOver = 32;
+constexpr int kBatchStreams = 4;
+// requests of one batch, at most
+constexpr int kBatchMaxRequests = 64;
 
 struct Request {
   uint64_t id = 0;
@@ -60,14 +80,18 @@ struct Request {
   std::vector<double> s;
   fj_opts opts{};
   size_t mem_est = 0;
+  int passed = 0;  // later requests admitted while this one did not fit
   // running state
   int slot = -1;
   int block_cap = 0;  // grid cap of the request's solve, fixed at admission
   fj_graph* own_graph = nullptr;
   fj_graph* building = nullptr;  // inline graph whose build is in flight (ev marks its end)
   char* dev = nullptr;  // one device allocation: s | quant | resid | status | workspace
-  cudaEvent_t ev = nullptr;
-  int launches = 0;
+  cudaEvent_t ev = nullptr;        // end of the current stage (build, or own solve)
+  cudaEvent_t ev_begin = nullptr;  // admission (start of the request's first GPU work)
+  cudaEvent_t ev_end = nullptr;    // completion (own, or the batch's)
+  bool in_batch = false;
+  int launches = 0;  // status entries (launches, or batch parts)
   // result
   bool done = false;
   fj_status rc = FJ_OK;
@@ -82,23 +106,34 @@ struct Slot {
   bool busy = false;
 };
 
+struct Batch {
+  cudaStream_t stream = nullptr;
+  bool busy = false;
+  std::vector<Request*> reqs;
+  cudaEvent_t ev = nullptr;
+};
+
 struct Server {
   int device = 0;
   int num_sms = 0;
   int max_inflight = 16;
   int64_t budget = 0;
   int max_blocks = 0;  // per-request grid cap (0: automatic, see block_cap)
+  int64_t pack_max_nodes = 1 << 17;  // graphs up to this size are batched (0: never)
   int64_t used = 0;
+  int admitted = 0;  // requests holding a slot (admitted, not yet retired)
   uint64_t next_id = 1;
   bool stop = false;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<Request*> pending;
-  std::vector<Request*> inflight;
+  std::list<Request*> pending;
+  std::vector<Request*> inflight;  // building or running on their own
+  std::vector<Request*> ready;     // small requests whose graph is resident, not yet batched
   std::unordered_map<uint64_t, Request*> all;
   std::deque<Slot> slots;  // grows in place: references to slots stay valid
+  Batch batches[kBatchStreams];
+  cudaEvent_t epoch = nullptr;  // device time origin of fj_info.t_begin_ms / t_end_ms
   std::thread worker;
-  std::string init_error;
 
   ~Server() {
     {
@@ -112,16 +147,21 @@ struct Server {
       if (sl.stream) cudaStreamDestroy(sl.stream);
       if (sl.pinned) cudaFreeHost(sl.pinned);
     }
+    for (auto& b : batches)
+      if (b.stream) cudaStreamDestroy(b.stream);
+    if (epoch) cudaEventDestroy(epoch);
     for (auto& kv : all) delete kv.second;
   }
 };
 
 namespace {
 
+int64_t request_n(const Request& r) { return r.graph ? r.graph->n : r.n; }
+
 size_t estimate_bytes(const Request& r, int num_sms) {
   // inline graph: sort buffers + CSR + sliced ELL, about 80 bytes per entry
   size_t b = 0;
-  int64_t n = r.graph ? r.graph->n : r.n;
+  const int64_t n = request_n(r);
   if (!r.graph) b += (size_t)(2 * r.m + 64) * 80 + (size_t)n * 64;
   const int K = std::min<int>(32, r.k);
   const int inner = r.opts.precision == FJ_PREC_FP64 ? 8 : 4;
@@ -137,6 +177,18 @@ int block_cap(const Server& S) {
   return std::max(1, 2 * S.num_sms / std::max(1, S.max_inflight));
 }
 
+// Launch widths of k columns: 32 at a time, then 16, 8, 4, 2, 1.
+int widths(int k, int* Ks) {
+  int count = 0;
+  for (int col = 0; col < k;) {
+    int K = 32;
+    while (K > k - col) K >>= 1;
+    Ks[count++] = K;
+    col += K;
+  }
+  return count;
+}
+
 void finish(Server& S, Request* r, fj_status rc) {
   r->rc = rc;
   r->done = true;
@@ -149,8 +201,8 @@ int64_t* build_words(Server& S, const Request* r) {
 }
 
 // Launches the request's own graph build on its slot's stream and records
-// r->ev after the copy of the build's host words; the solve starts once that
-// event has completed (start_solve), so the worker thread never waits for a
+// r->ev after the copy of the build's host words; the request becomes ready
+// once that event has completed, so the worker thread never waits for a
 // build.  Returns an error code if it could not be started.
 fj_status start_build(Server& S, Request* r) {
   Slot& sl = S.slots[r->slot];
@@ -174,7 +226,8 @@ fj_status start_build(Server& S, Request* r) {
   }
   fj_graph* pending = nullptr;
   fj_status rc = fj_build_graph_begin(S.device, st, r->n, r->m, ds, dd, r->weighted ? dw : nullptr,
-                                      (r->opts.flags & FJ_MERGE_DUPLICATES) != 0, build_words(S, r), &pending);
+                                      (r->opts.flags & FJ_MERGE_DUPLICATES) != 0, Layout(), build_words(S, r),
+                                      &pending);
   cudaFreeAsync(ds, st);
   cudaFreeAsync(dd, st);
   if (dw) cudaFreeAsync(dw, st);
@@ -185,34 +238,33 @@ fj_status start_build(Server& S, Request* r) {
   return FJ_OK;
 }
 
-// Launches the solve on the slot's stream (the graph is resident: the
-// caller's, or the request's own once its build has ended).
+// Ends the build of an inline graph (its event has completed): the graph
+// becomes the request's own, and its host edge list is dropped.
+fj_status end_build(Server& S, Request* r) {
+  fj_graph* og = nullptr;
+  fj_graph* g0 = r->building;
+  r->building = nullptr;
+  cudaEventDestroy(r->ev);
+  r->ev = nullptr;
+  fj_status rc = fj_build_graph_end(g0, build_words(S, r), S.slots[r->slot].stream, &og);
+  if (rc != FJ_OK) return rc;
+  r->own_graph = og;
+  std::vector<int32_t>().swap(r->src);
+  std::vector<int32_t>().swap(r->dst);
+  std::vector<float>().swap(r->w);
+  return FJ_OK;
+}
+
+// Launches the request's own solve on its slot's stream (the graph is
+// resident: the caller's, or the request's own).
 fj_status start_solve(Server& S, Request* r) {
   Slot& sl = S.slots[r->slot];
   cudaStream_t st = sl.stream;
   cudaSetDevice(S.device);
-  if (r->building) {
-    fj_graph* og = nullptr;
-    fj_graph* g0 = r->building;
-    r->building = nullptr;
-    cudaEventDestroy(r->ev);
-    r->ev = nullptr;
-    fj_status rc = fj_build_graph_end(g0, build_words(S, r), st, &og);
-    if (rc != FJ_OK) return rc;
-    r->own_graph = og;
-    std::vector<int32_t>().swap(r->src);
-    std::vector<int32_t>().swap(r->dst);
-    std::vector<float>().swap(r->w);
-  }
   const fj_graph* g = r->graph ? r->graph : r->own_graph;
   const int64_t n = g->n;
-  int Ks[64], launches = 0;
-  for (int col = 0; col < r->k;) {
-    int K = 32;
-    while (K > r->k - col) K >>= 1;
-    Ks[launches++] = K;
-    col += K;
-  }
+  int Ks[64];
+  const int launches = widths(r->k, Ks);
   const int inner = r->opts.precision == FJ_PREC_FP64 ? 8 : 4;
   size_t ws = 0;
   for (int i = 0; i < launches; ++i) ws = std::max(ws, fj_solve_workspace_bytes(g, Ks[i], inner, S.num_sms));
@@ -238,9 +290,152 @@ fj_status start_solve(Server& S, Request* r) {
   cudaFreeAsync(r->dev, st);
   r->dev = nullptr;
   if (r->own_graph) fj_free_graph_arrays(r->own_graph, st);
-  cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
+  cudaEventCreate(&r->ev);
   cudaEventRecord(r->ev, st);
+  r->ev_end = r->ev;
   std::vector<double>().swap(r->s);
+  return FJ_OK;
+}
+
+// Solves the requests of batch B together on its stream: each request's
+// parts (launches of 32/16/8/4/2/1 columns), grouped by width, are packed
+// into shared persistent launches, each part on its own block range of at
+// most the request's grid cap.  Per request, the small outputs keep the
+// layout of an own solve (quant | resid | status per part), so collect()
+// reads them the same way.
+fj_status start_batch(Server& S, Batch& B) {
+  cudaStream_t st = B.stream;
+  cudaSetDevice(S.device);
+  struct Part {
+    int req, col, K, blocks;
+    size_t ws;
+  };
+  const int prec = B.reqs[0]->opts.precision;
+  std::vector<Part> parts;
+  std::vector<size_t> base(B.reqs.size());
+  size_t off = 0;
+  for (size_t i = 0; i < B.reqs.size(); ++i) {
+    Request* r = B.reqs[i];
+    const int64_t n = (r->graph ? r->graph : r->own_graph)->n;
+    int Ks[64];
+    r->launches = widths(r->k, Ks);
+    base[i] = off;
+    off += ((size_t)n * r->k * 8 + 255) & ~size_t(255);
+    off += ((size_t)r->k * 6 * 8 + (size_t)r->launches * 12 + 255) & ~size_t(255);
+  }
+  const size_t bars_off = off;
+  off += 64 * FJ_PACK_MAX;
+  // parts by width, then packs
+  const int inner = prec == FJ_PREC_FP64 ? 8 : 4;
+  size_t ws_need = 0;
+  std::vector<std::vector<std::pair<int, int>>> packs_of_width;
+  std::vector<int> width_begin;
+  for (int K : {32, 16, 8, 4, 2, 1}) {
+    int cap = 0;
+    fj_status rc = fj_pack_capacity(prec, K, S.num_sms, &cap);
+    if (rc != FJ_OK) return rc;
+    const int begin = (int)parts.size();
+    for (size_t i = 0; i < B.reqs.size(); ++i) {
+      Request* r = B.reqs[i];
+      const fj_graph* g = r->graph ? r->graph : r->own_graph;
+      int Ks[64];
+      const int nw = widths(r->k, Ks);
+      int col = 0;
+      for (int j = 0; j < nw; ++j) {
+        if (Ks[j] == K) {
+          const int b = fj_pack_blocks(g, K, std::min(cap, r->block_cap));
+          parts.push_back({(int)i, col, K, b, fj_solve_workspace_bytes_blocks(g, K, inner, b)});
+        }
+        col += Ks[j];
+      }
+    }
+    std::vector<int> blocks;
+    for (int j = begin; j < (int)parts.size(); ++j) blocks.push_back(parts[j].blocks);
+    std::vector<std::pair<int, int>> packs = plan_packs(blocks, cap);
+    for (auto& pr : packs) {
+      pr.first += begin;
+      pr.second += begin;
+      size_t sum = 0;
+      for (int j = pr.first; j < pr.second; ++j) sum += (parts[j].ws + 255) & ~size_t(255);
+      ws_need = std::max(ws_need, sum);
+    }
+    packs_of_width.push_back(packs);
+  }
+  const size_t ws_off = off;
+  char* dev = nullptr;
+  if (malloc_async(&dev, ws_off + ws_need, st) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("fj_submit: out of device memory for a batch");
+    return FJ_ERR_OOM;
+  }
+  // inputs
+  for (size_t i = 0; i < B.reqs.size(); ++i) {
+    Request* r = B.reqs[i];
+    const int64_t n = (r->graph ? r->graph : r->own_graph)->n;
+    cudaMemcpyAsync(dev + base[i], r->s.data(), (size_t)n * r->k * 8, cudaMemcpyHostToDevice, st);
+    char* small = dev + base[i] + (((size_t)n * r->k * 8 + 255) & ~size_t(255));
+    cudaMemsetAsync(small + (size_t)r->k * 6 * 8, 0, (size_t)r->launches * 12, st);
+  }
+  // the packed launches; a request's part index counts its widths in the
+  // order of its own launches (32, 16, ..., 1), as in an own solve.  The
+  // batch's requests share a precision; tolerances and caps are their own.
+  fj_opts o = B.reqs[0]->opts;
+  o.flags = FJ_DEVICE_PTRS;
+  std::vector<PackItem> items;
+  for (const auto& packs : packs_of_width) {
+    for (const auto& pr : packs) {
+      items.clear();
+      size_t woff = 0;
+      for (int j = pr.first; j < pr.second; ++j) {
+        const Part& pt = parts[j];
+        Request* r = B.reqs[pt.req];
+        const fj_graph* g = r->graph ? r->graph : r->own_graph;
+        const int64_t n = g->n;
+        char* sbase = dev + base[pt.req];
+        double* dq = (double*)(sbase + (((size_t)n * r->k * 8 + 255) & ~size_t(255)));
+        int Ks[64];
+        const int nw = widths(r->k, Ks);
+        int pidx = 0, c = 0;
+        for (; pidx < nw && c != pt.col; ++pidx) c += Ks[pidx];
+        PackItem it;
+        it.g = g;
+        it.s = (const double*)sbase + (int64_t)pt.col * n;
+        it.ld = n;
+        it.z = nullptr;
+        it.quant = dq + (size_t)pt.col * 5;
+        it.resid = dq + (size_t)r->k * 5 + pt.col;
+        it.status = (int*)(dq + (size_t)r->k * 6) + 3 * pidx;
+        it.ws = dev + ws_off + woff;
+        it.ws_bytes = pt.ws;
+        it.blocks = pt.blocks;
+        it.opts = r->opts;
+        it.opts.flags = FJ_DEVICE_PTRS;
+        woff += (pt.ws + 255) & ~size_t(255);
+        r->info.blocks = std::max(r->info.blocks, pt.blocks);
+        items.push_back(it);
+      }
+      fj_status rc = fj_solve_packed_device(parts[pr.first].K, (int)items.size(), items.data(), st, o,
+                                            dev + bars_off);
+      if (rc != FJ_OK) {
+        cudaFreeAsync(dev, st);
+        return rc;
+      }
+    }
+  }
+  // results into each request's pinned slot buffer, then release
+  for (size_t i = 0; i < B.reqs.size(); ++i) {
+    Request* r = B.reqs[i];
+    const int64_t n = (r->graph ? r->graph : r->own_graph)->n;
+    char* small = dev + base[i] + (((size_t)n * r->k * 8 + 255) & ~size_t(255));
+    cudaMemcpyAsync(S.slots[r->slot].pinned, small, (size_t)r->k * 6 * 8 + (size_t)r->launches * 12,
+                    cudaMemcpyDeviceToHost, st);
+    if (r->own_graph) fj_free_graph_arrays(r->own_graph, st);
+    std::vector<double>().swap(r->s);
+  }
+  cudaFreeAsync(dev, st);
+  cudaEventCreate(&B.ev);
+  cudaEventRecord(B.ev, st);
+  for (Request* r : B.reqs) r->ev_end = B.ev;
   return FJ_OK;
 }
 
@@ -272,12 +467,23 @@ void collect(Server& S, Request* r) {
   r->info.warnings = (bits & kWarnOpinionRange) ? FJ_WARN_OPINION_RANGE : 0u;
   r->info.device_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - r->t_start).count();
+  float a = 0.f, b = 0.f;
+  if (r->ev_begin && r->ev_end && cudaEventElapsedTime(&a, S.epoch, r->ev_begin) == cudaSuccess &&
+      cudaEventElapsedTime(&b, S.epoch, r->ev_end) == cudaSuccess) {
+    r->info.t_begin_ms = a;
+    r->info.t_end_ms = b;
+  }
+  cudaGetLastError();
+  r->info.batched = r->in_batch ? 1 : 0;
   if (r->own_graph) {
     delete r->own_graph;  // arrays were freed stream-ordered at launch time
     r->own_graph = nullptr;
   }
-  cudaEventDestroy(r->ev);
+  if (!r->in_batch && r->ev) cudaEventDestroy(r->ev);
   r->ev = nullptr;
+  r->ev_end = nullptr;
+  if (r->ev_begin) cudaEventDestroy(r->ev_begin);
+  r->ev_begin = nullptr;
   finish(S, r, rc);
 }
 
@@ -287,6 +493,7 @@ void abandon(Server& S, Request* r, fj_status rc) {
   cudaStream_t st = S.slots[r->slot].stream;
   S.slots[r->slot].busy = false;
   S.used -= (int64_t)r->mem_est;
+  --S.admitted;
   if (r->own_graph) {
     fj_free_graph_arrays(r->own_graph, st);
     delete r->own_graph;
@@ -296,12 +503,32 @@ void abandon(Server& S, Request* r, fj_status rc) {
     cudaFreeAsync(r->dev, st);
     r->dev = nullptr;
   }
-  if (r->ev) {
-    cudaEventDestroy(r->ev);
-    r->ev = nullptr;
-  }
+  if (r->ev && !r->in_batch) cudaEventDestroy(r->ev);
+  r->ev = nullptr;
+  if (r->ev_begin) cudaEventDestroy(r->ev_begin);
+  r->ev_begin = nullptr;
+  r->ev_end = nullptr;
   finish(S, r, rc);
   S.cv_done.notify_all();
+}
+
+bool small_request(const Server& S, const Request* r) {
+  return S.pack_max_nodes > 0 && request_n(*r) <= S.pack_max_nodes;
+}
+
+// A request whose graph is resident: small ones wait for the next batch,
+// others start their own solve.  Returns an error code if it could not be
+// started.
+fj_status on_ready(Server& S, Request* r, std::unique_lock<std::mutex>& lock) {
+  if (small_request(S, r)) {
+    S.ready.push_back(r);
+    return FJ_OK;
+  }
+  lock.unlock();
+  const fj_status rc = start_solve(S, r);
+  lock.lock();
+  if (rc == FJ_OK) S.inflight.push_back(r);
+  return rc;
 }
 
 void worker_loop(Server* Sp) {
@@ -311,8 +538,8 @@ void worker_loop(Server* Sp) {
   while (true) {
     if (S.stop) break;
     bool progress = false;
-    // requests whose graph build ended start their solve; finished requests
-    // retire (only this thread changes the in-flight list)
+    // builds that ended make their request ready; own solves that ended
+    // retire (only this thread changes these lists)
     for (size_t i = 0; i < S.inflight.size();) {
       Request* r = S.inflight[i];
       if (cudaEventQuery(r->ev) != cudaSuccess) {
@@ -320,52 +547,131 @@ void worker_loop(Server* Sp) {
         continue;
       }
       progress = true;
+      S.inflight.erase(S.inflight.begin() + i);
       if (r->building) {
         lock.unlock();
-        const fj_status rc = start_solve(S, r);
+        fj_status rc = end_build(S, r);
         lock.lock();
-        if (rc == FJ_OK) {
-          ++i;
-          continue;
-        }
-        abandon(S, r, rc);
-      } else {
+        if (rc == FJ_OK) rc = on_ready(S, r, lock);
+        if (rc != FJ_OK) abandon(S, r, rc);
+        continue;
+      }
+      collect(S, r);
+      S.slots[r->slot].busy = false;
+      S.used -= (int64_t)r->mem_est;
+      --S.admitted;
+    }
+    // batches that ended retire their requests
+    for (Batch& B : S.batches) {
+      if (!B.busy || cudaEventQuery(B.ev) != cudaSuccess) continue;
+      progress = true;
+      for (Request* r : B.reqs) {
         collect(S, r);
         S.slots[r->slot].busy = false;
         S.used -= (int64_t)r->mem_est;
+        --S.admitted;
       }
-      S.inflight.erase(S.inflight.begin() + i);
+      B.reqs.clear();
+      cudaEventDestroy(B.ev);
+      B.ev = nullptr;
+      B.busy = false;
     }
     if (progress) S.cv_done.notify_all();
-    // admit in arrival order while a slot and the memory budget allow
-    while (!S.pending.empty() && (int)S.inflight.size() < S.max_inflight) {
-      Request* r = S.pending.front();
-      if (S.used + (int64_t)r->mem_est > S.budget && !S.inflight.empty()) break;
-      S.pending.pop_front();
+    // ready small requests go out as a batch on a free batch stream
+    // (grouped by precision: one batch holds one precision)
+    for (Batch& B : S.batches) {
+      if (S.ready.empty()) break;
+      if (B.busy) continue;
+      const int prec = S.ready.front()->opts.precision;
+      for (size_t i = 0; i < S.ready.size() && (int)B.reqs.size() < kBatchMaxRequests;) {
+        if (S.ready[i]->opts.precision == prec) {
+          B.reqs.push_back(S.ready[i]);
+          S.ready.erase(S.ready.begin() + i);
+        } else {
+          ++i;
+        }
+      }
+      for (Request* r : B.reqs) r->in_batch = true;
+      B.busy = true;
+      lock.unlock();
+      const fj_status rc = start_batch(S, B);
+      lock.lock();
+      if (rc != FJ_OK) {
+        for (Request* r : B.reqs) abandon(S, r, rc);
+        B.reqs.clear();
+        B.busy = false;
+      }
+      progress = true;
+    }
+    // admission: in arrival order; a request that does not fit yet is passed
+    // over by later ones at most kMaxPassOver times
+    Request* blocked = nullptr;
+    for (auto it = S.pending.begin(); it != S.pending.end() && S.admitted < S.max_inflight;) {
+      Request* r = *it;
+      if (S.used + (int64_t)r->mem_est > S.budget && S.admitted > 0) {
+        if (!blocked) blocked = r;
+        if (blocked->passed >= kMaxPassOver) break;
+        ++it;
+        continue;
+      }
+      if (blocked) {
+        if (blocked->passed >= kMaxPassOver) break;
+        ++blocked->passed;
+      }
+      it = S.pending.erase(it);
       int slot = 0;
       while (S.slots[slot].busy) ++slot;
       S.slots[slot].busy = true;
       r->slot = slot;
       r->block_cap = block_cap(S);
       S.used += (int64_t)r->mem_est;
+      ++S.admitted;
       r->t_start = std::chrono::steady_clock::now();
-      lock.unlock();
-      const fj_status rc = r->graph ? start_solve(S, r) : start_build(S, r);
-      lock.lock();
-      if (rc != FJ_OK)
-        abandon(S, r, rc);
-      else
-        S.inflight.push_back(r);
+      cudaEventCreate(&r->ev_begin);
+      cudaEventRecord(r->ev_begin, S.slots[slot].stream);
+      fj_status rc = FJ_OK;
+      if (r->graph) {
+        rc = on_ready(S, r, lock);
+      } else {
+        lock.unlock();
+        rc = start_build(S, r);
+        lock.lock();
+        if (rc == FJ_OK) S.inflight.push_back(r);
+      }
+      if (rc != FJ_OK) abandon(S, r, rc);
       progress = true;
     }
     if (!progress) {
-      if (S.inflight.empty() && S.pending.empty())
+      bool busy = !S.inflight.empty() || !S.ready.empty();
+      for (auto& B : S.batches) busy |= B.busy;
+      if (!busy && S.pending.empty())
         S.cv_work.wait(lock);
       else
         S.cv_work.wait_for(lock, std::chrono::microseconds(20));
     }
   }
   // shutdown: drain what is on the GPU, drop what is queued
+  for (Batch& B : S.batches) {
+    if (!B.busy) continue;
+    cudaStreamSynchronize(B.stream);
+    for (Request* r : B.reqs) collect(S, r);
+    B.reqs.clear();
+    cudaEventDestroy(B.ev);
+    B.ev = nullptr;
+    B.busy = false;
+  }
+  for (Request* r : S.ready) {
+    if (r->own_graph) {
+      fj_free_graph_arrays(r->own_graph, S.slots[r->slot].stream);
+      cudaStreamSynchronize(S.slots[r->slot].stream);
+      delete r->own_graph;
+      r->own_graph = nullptr;
+    }
+    if (r->ev_begin) cudaEventDestroy(r->ev_begin);
+    r->ev_begin = nullptr;
+    finish(S, r, FJ_ERR_ARG);
+  }
+  S.ready.clear();
   for (Request* r : S.inflight) {
     cudaStreamSynchronize(S.slots[r->slot].stream);
     if (r->building) {  // a build that ended: drop its graph
@@ -377,6 +683,8 @@ void worker_loop(Server* Sp) {
       r->building = nullptr;
       cudaEventDestroy(r->ev);
       r->ev = nullptr;
+      if (r->ev_begin) cudaEventDestroy(r->ev_begin);
+      r->ev_begin = nullptr;
       cudaStreamSynchronize(S.slots[r->slot].stream);
       finish(S, r, FJ_ERR_ARG);
       continue;
@@ -408,6 +716,18 @@ Server* server_create(int device, int num_sms) {
       return nullptr;
     }
   }
+  for (auto& B : S->batches) {
+    if (cudaStreamCreateWithFlags(&B.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete S;
+      return nullptr;
+    }
+  }
+  if (cudaEventCreate(&S->epoch) != cudaSuccess || cudaEventRecord(S->epoch, S->slots[0].stream) != cudaSuccess) {
+    cudaGetLastError();
+    delete S;
+    return nullptr;
+  }
   S->worker = std::thread(worker_loop, S);
   return S;
 }
@@ -435,6 +755,13 @@ fj_status server_config(Server* S, int32_t max_inflight, int64_t budget, int32_t
   }
   if (budget > 0) S->budget = budget;
   if (max_blocks >= 0) S->max_blocks = max_blocks;
+  S->cv_work.notify_all();
+  return FJ_OK;
+}
+
+fj_status server_pack(Server* S, int64_t max_nodes) {
+  std::lock_guard<std::mutex> lock(S->mu);
+  S->pack_max_nodes = max_nodes;
   S->cv_work.notify_all();
   return FJ_OK;
 }

@@ -90,7 +90,7 @@ struct SolveParams {
   VI* p;
   VI* d;
   VI* t;
-  double* part;  // [gridDim][NSLOT][K]
+  double* part;  // [blocks][NSLOT][K]
   Barrier* bar;
   // options
   double tol;
@@ -109,29 +109,26 @@ struct SolveParams {
   // failure-detection test's stuck block)
   uint64_t timeout_ns;
   unsigned withhold;
-  // rows of the walks' gathered vectors kept in L2 (loaded and stored
-  // normally while everything else is streamed): of the inner iterate u and
-  // of the refined iterate q
-  int32_t hot_inner;
-  int32_t hot_ref;
 };
 
-// Grid-wide barrier with a bounded wait.  The counter only grows: barrier
-// number e of a launch completes when it reaches e * gridDim.x.  Arrival is
+// Barrier of one problem's nb blocks (bid = this block's index among them;
+// the whole grid, or one problem's block range of a packed launch) with a
+// bounded wait.  The counter only grows: barrier number e of a solve
+// completes when it reaches e * nb.  Arrival is
 // one release-reduction per block (publishing the block's writes, ordered
 // before it by __syncthreads); the wait polls with acquire loads.  Returns
 // false once any block has given up (error bit kErrTimeout), after which every
 // later barrier returns at once so that all blocks leave the kernel.
 __device__ __forceinline__ bool grid_sync(Barrier* bar, int* status, unsigned& epoch, uint64_t timeout_ns,
-                                          unsigned withhold) {
+                                          unsigned withhold, int bid, int nb) {
   __shared__ int ok_sh;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = (ld_volatile_i32(status) & kErrTimeout) == 0;
-    if (gridDim.x > 1 && ok) {
+    if (nb > 1 && ok) {
       ++epoch;
-      const unsigned target = epoch * gridDim.x;
-      if (!(epoch == withhold && blockIdx.x == 0))
+      const unsigned target = epoch * (unsigned)nb;
+      if (!(epoch == withhold && bid == 0))
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
       if (ld_acquire_u32(&bar->count) < target) {
         const uint64_t t0 = global_ns();
@@ -157,7 +154,7 @@ __device__ __forceinline__ bool grid_sync(Barrier* bar, int* status, unsigned& e
 // c = tid % K), stored as this block's partials for the given slots.
 template <int K, int NS, bool kMax = false>
 __device__ __forceinline__ void block_store(const double (&v)[NS], const int (&slots)[NS],
-                                            double* part, double* red /*[NS][kWarps][K]*/) {
+                                            double* part, double* red /*[NS][kWarps][K]*/, int bid) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();  // red aliases the walks' shared staging
 #pragma unroll
@@ -179,7 +176,7 @@ __device__ __forceinline__ void block_store(const double (&v)[NS], const int (&s
       const double y = red[(j * kWarps + w) * K + c];
       s = kMax ? fmax(s, y) : s + y;
     }
-    part[((int64_t)blockIdx.x * NSLOT + slots[j]) * K + c] = s;
+    part[((int64_t)bid * NSLOT + slots[j]) * K + c] = s;
   }
   __syncthreads();
 }
@@ -188,12 +185,12 @@ __device__ __forceinline__ void block_store(const double (&v)[NS], const int (&s
 // partials, in block order, identically in every block.
 template <int K, int NS, bool kMax = false>
 __device__ __forceinline__ void grid_reduce(const int (&slots)[NS], const double* part,
-                                            double* res /*[NSLOT][K]*/) {
+                                            double* res /*[NSLOT][K]*/, int nb) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int e = warp; e < NS * K; e += kWarps) {
     const int slot = slots[e / K], c = e % K;
     double s = kMax ? -INFINITY : 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
+    for (int b = lane; b < nb; b += 32) {
       const double y = __ldcg(&part[((int64_t)b * NSLOT + slot) * K + c]);
       s = kMax ? fmax(s, y) : s + y;
     }
@@ -222,7 +219,7 @@ template <typename T, int K>
 __device__ __forceinline__ void wide_walk(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
                                           T* __restrict__ part,
                                           unsigned long long* counter, unsigned long long base,
-                                          double* __restrict__ quad_u, T* __restrict__ sxr, int32_t hot) {
+                                          double* __restrict__ quad_u, T* __restrict__ sxr) {
   const int lane = threadIdx.x & 31;
   while (true) {
     unsigned long long k = 0;
@@ -230,7 +227,7 @@ __device__ __forceinline__ void wide_walk(const SellGraph& g, const T* __restric
     const int64_t u = (int64_t)__shfl_sync(kFull, k, 0);
     if (u >= g.n_units) break;
     T q = num<T>(0.f);
-    wide_unit<T, K>(g, x, out, part, u, q, sxr, hot);
+    wide_unit<T, K>(g, x, out, part, u, q, sxr);
     double qd = to_double(q);
 #pragma unroll
     for (int off = K; off < 32; off <<= 1) qd += __shfl_xor_sync(kFull, qd, off);
@@ -268,8 +265,12 @@ __device__ __forceinline__ double lane_share(T (&v)[K]) {
   return mine;
 }
 
+// The whole solve of one problem on nb blocks; bid = this block's index
+// among them.  Every grid-wide step (barriers, reductions, work splits) is
+// over those nb blocks only, so a problem's results depend on nb alone, not
+// on the launch it runs in.
 template <typename VI, int K>
-__global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
+__device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int bid, const int nb) {
   using VR = typename SolveParams<VI>::VR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* red = reinterpret_cast<double*>(smem_raw);  // [7][kWarps][K], aliases the staging
@@ -283,8 +284,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   const int warp = threadIdx.x >> 5;
   const int64_t n = P.sg.n;
   const int64_t NK = n * K;
-  const int64_t gtid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  const int64_t gstride = (int64_t)gridDim.x * kThreads;
+  const int64_t gtid = (int64_t)bid * kThreads + threadIdx.x;
+  const int64_t gstride = (int64_t)nb * kThreads;
   const int c = threadIdx.x % K;
   // per-warp staging of the wide walks' row values
   VI* my_sxr = reinterpret_cast<VI*>(smem_raw + warp * kWideStageBytes);
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   int* status = P.status;
   const bool fp32_mode = P.mode == kModeFP32;
   unsigned epoch = 0;  // barriers passed (used by thread 0)
-  auto sync = [&]() { return grid_sync(P.bar, status, epoch, P.timeout_ns, P.withhold); };
+  auto sync = [&]() { return grid_sync(P.bar, status, epoch, P.timeout_ns, P.withhold, bid, nb); };
   // every K walks the same work units (sliced ELL for K <= 4, lanes as
   // columns for K >= 8), so all row sums are complete after a walk
   constexpr bool kWide = K >= 8;
@@ -301,26 +302,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   // kernels from spilling)
   constexpr int kInnerBatch = (sizeof(VI) == 4 && K <= 2) ? 8 : 4;
   constexpr int kResidBatch = (sizeof(VI) == 4 && K == 1) ? 8 : 4;
+  // narrow kernels stream the vectors of the update pass (evict-first), so
+  // that the walk's gathered vector stays in L2; the wide kernels keep
+  // plain loads and stores, which measured faster there
+  constexpr bool kStream = K <= 4;
+  auto vld = [](const VI* a) -> VI {
+    if constexpr (kStream) return ld_cs(a);
+    else return *a;
+  };
+  auto vst = [](VI* a, VI v) {
+    if constexpr (kStream) st_cs(a, v);
+    else *a = v;
+  };
 
   // K <= 4: this warp's share of the work units, split by cost;
   // K >= 8: the units whose edge sums this block adds up (even split)
   int64_t u0 = 0, u1 = 0;
   unsigned long long unit_base = 0;  // unit counter at the start of the next wide walk
   if constexpr (kWide) {
-    u0 = P.sg.n_units * (int64_t)blockIdx.x / gridDim.x;
-    u1 = P.sg.n_units * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    u0 = P.sg.n_units * (int64_t)bid / nb;
+    u1 = P.sg.n_units * (int64_t)(bid + 1) / nb;
   } else {
     // range wr of W: consecutive ranges (units of similar kind) go to
     // different blocks, so that every SM gets a mix of hub chunks and slices
     const int lane = threadIdx.x & 31;
-    const int64_t W = (int64_t)gridDim.x * kWarps;
-    const int64_t wr = (int64_t)warp * gridDim.x + blockIdx.x;
+    const int64_t W = (int64_t)nb * kWarps;
+    const int64_t wr = (int64_t)warp * nb + bid;
     int64_t v = 0;
     if (lane < 2) v = sell_unit_start(P.sg, wr + lane, W);
     u0 = __shfl_sync(kFull, v, 0);
     u1 = __shfl_sync(kFull, v, 1);
   }
-  const unsigned long long unit_step = (unsigned long long)P.sg.n_units + (unsigned long long)gridDim.x * kWarps;
+  const unsigned long long unit_step = (unsigned long long)P.sg.n_units + (unsigned long long)nb * kWarps;
 
   // ---------------------------------------------------------------- setup
   {
@@ -338,17 +351,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
     if (__syncthreads_or(outside) && threadIdx.x == 0) atomicOr(status, kWarnOpinionRange);
     const double v[1] = {acc};
     const int sl[1] = {S_SUM};
-    block_store<K, 1>(v, sl, P.part, red);
+    block_store<K, 1>(v, sl, P.part, red, bid);
     const double vm[2] = {mx, nmn};
     const int slm[2] = {S_MAX, S_NMIN};
-    block_store<K, 2, true>(vm, slm, P.part, red);
+    block_store<K, 2, true>(vm, slm, P.part, red, bid);
   }
   if (!sync()) return;
   {
     const int sl[1] = {S_SUM};
-    grid_reduce<K, 1>(sl, P.part, res);
+    grid_reduce<K, 1>(sl, P.part, res, nb);
     const int slm[2] = {S_MAX, S_NMIN};
-    grid_reduce<K, 2, true>(slm, P.part, res);
+    grid_reduce<K, 2, true>(slm, P.part, res, nb);
     if (threadIdx.x < K) {
       const int cc = threadIdx.x;
       // a column solved as is (two-solve mode, even columns) keeps mu = 0
@@ -372,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   auto residual_walk = [&]() -> bool {
     double quad;
     if constexpr (kWide) {
-      wide_walk<VR, K>(P.sg, P.q, P.t64, P.hub_part64, P.unit_counter, unit_base, P.quad_u, my_sxr64, P.hot_ref);
+      wide_walk<VR, K>(P.sg, P.q, P.t64, P.hub_part64, P.unit_counter, unit_base, P.quad_u, my_sxr64);
       unit_base += unit_step;
       if (!sync()) return false;
       quad = unit_sum<K>(P.quad_u, u0, u1);
@@ -380,12 +393,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       VR qd[K];
 #pragma unroll
       for (int cc = 0; cc < K; ++cc) qd[cc] = num<VR>(0.0f);
-      sell_walk<VR, K, kResidBatch>(P.sg, P.q, P.t64, P.hub_part64, u0, u1, qd, P.hot_ref);
+      sell_walk<VR, K, kResidBatch>(P.sg, P.q, P.t64, P.hub_part64, u0, u1, qd);
       quad = lane_share<VR, K>(qd);
     }
     const double v[1] = {quad};
     const int sl[1] = {S_D};
-    block_store<K, 1>(v, sl, P.part, red);
+    block_store<K, 1>(v, sl, P.part, red, bid);
     return sync();
   };
 
@@ -443,12 +456,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         a_ci += dq * dq;
         const VI rv = to_inner<VI>(r64);
         const VI uv = P.dinv[i] * rv;
-        st_cs(P.x + idx, VI(0));
-        st_cs(P.r + idx, rv);
-        if (i < P.hot_inner)
-          P.u[idx] = uv;
-        else
-          st_cs(P.u + idx, uv);
+        vst(P.x + idx, VI(0));
+        vst(P.r + idx, rv);
+        P.u[idx] = uv;
         a_gam += (double)(rv * uv);
         a_rr += (double)(rv * rv);
         a_uu += (double)(uv * uv);
@@ -456,24 +466,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       const double v[7] = {to_double(a_rr64), to_double(a_p), to_double(a_qs), to_double(a_ci),
                            a_gam, a_rr, a_uu};
       const int sl[7] = {S_RR64, S_P, S_QS, S_CI, S_GAM, S_RR, S_UU};
-      block_store<K, 7>(v, sl, P.part, red);
+      block_store<K, 7>(v, sl, P.part, red, bid);
       if (init) {
         const double vb[1] = {a_bb};
         const int sb[1] = {S_BB};
-        block_store<K, 1>(vb, sb, P.part, red);
+        block_store<K, 1>(vb, sb, P.part, red, bid);
       }
     }
     if (!sync()) return;
     {
       const int sl[7] = {S_RR64, S_P, S_QS, S_CI, S_GAM, S_RR, S_UU};
-      grid_reduce<K, 7>(sl, P.part, res);
+      grid_reduce<K, 7>(sl, P.part, res, nb);
       if (init) {
         const int sb[1] = {S_BB};
-        grid_reduce<K, 1>(sb, P.part, res);
+        grid_reduce<K, 1>(sb, P.part, res, nb);
       }
       if (!init || warm) {
         const int sd[1] = {S_D};
-        grid_reduce<K, 1>(sd, P.part, res);
+        grid_reduce<K, 1>(sd, P.part, res, nb);
       }
     }
     if (threadIdx.x == 0) ctl_stop = 0;
@@ -486,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       if (!finite(rr64)) atomicOr(status, kErrNumeric);
       // quantities of the current iterate (final after the last pass),
       // scaled back: squares by 2^2e, 1^T q by 2^e
-      if (blockIdx.x == 0) {
+      if (bid == 0) {
         const int e2 = 2 * ex[cc];
         const double m = mu[cc];
         const double D = (init && !warm) ? 0.0 : ldexp(0.5 * res[S_D * K + cc], e2);
@@ -540,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
       {
         double qv;
         if constexpr (kWide) {
-          wide_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.unit_counter, unit_base, P.quad_u, my_sxr, P.hot_inner);
+          wide_walk<VI, K>(P.sg, P.u, P.t, P.hub_part, P.unit_counter, unit_base, P.quad_u, my_sxr);
           unit_base += unit_step;
           if (!sync()) return;
           qv = unit_sum<K>(P.quad_u, u0, u1);
@@ -548,17 +558,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
           VI quad[K];
 #pragma unroll
           for (int cc = 0; cc < K; ++cc) quad[cc] = VI(0);
-          sell_walk<VI, K, kInnerBatch>(P.sg, P.u, P.t, P.hub_part, u0, u1, quad, P.hot_inner);
+          sell_walk<VI, K, kInnerBatch>(P.sg, P.u, P.t, P.hub_part, u0, u1, quad);
           qv = lane_share<VI, K>(quad);
         }
         const double v[1] = {qv};
         const int sl[1] = {S_EQ};
-        block_store<K, 1>(v, sl, P.part, red);
+        block_store<K, 1>(v, sl, P.part, red, bid);
       }
       if (!sync()) return;
       {
         const int sl[1] = {S_EQ};
-        grid_reduce<K, 1>(sl, P.part, res);
+        grid_reduce<K, 1>(sl, P.part, res, nb);
       }
       if (threadIdx.x < K) {
         const int cc = threadIdx.x;
@@ -604,9 +614,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         VI* __restrict__ vu = P.u;
         const VI* __restrict__ vt = P.t;
         const float* __restrict__ vdinv = P.dinv;
-        // the new u is the next walk's gathered vector: kept in L2 for rows
-        // below hot_inner, the other vectors streamed
-        const int64_t hot_idx = (int64_t)P.hot_inner * K;
+        // the new u is the next walk's gathered vector: stored normally (it
+        // stays in L2), the other vectors streamed in the narrow kernels
         // kV elements per thread per round, all loads issued before use
         constexpr int kV = 2;
         for (int64_t base = gtid; base < NK; base += kV * gstride) {
@@ -616,13 +625,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
             const int64_t idx = base + e * gstride;
             if (idx < NK) {
               const int64_t i = idx / K;
-              uv[e] = ld_cs(vu + idx);
+              uv[e] = vld(vu + idx);
               tv[e] = row_t<VI, K>(P.sg, vt, P.hub_part, i, idx, c);
-              pv[e] = fst ? VI(0) : ld_cs(vp + idx);
-              dv[e] = fst ? VI(0) : ld_cs(vd + idx);
-              xv[e] = ld_cs(vx + idx);
-              rv[e] = ld_cs(vr + idx);
-              di[e] = ld_ro(vdinv + i);
+              pv[e] = fst ? VI(0) : vld(vp + idx);
+              dv[e] = fst ? VI(0) : vld(vd + idx);
+              xv[e] = vld(vx + idx);
+              rv[e] = vld(vr + idx);
+              di[e] = kStream ? ld_ro(vdinv + i) : vdinv[i];
             }
           }
 #pragma unroll
@@ -635,14 +644,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
               const VI xn = xv[e] + al * pn;
               const VI rn = rv[e] - al * dn;
               const VI un = di[e] * rn;
-              st_cs(vp + idx, pn);
-              st_cs(vd + idx, dn);
-              st_cs(vx + idx, xn);
-              st_cs(vr + idx, rn);
-              if (idx < hot_idx)
-                vu[idx] = un;
-              else
-                st_cs(vu + idx, un);
+              vst(vp + idx, pn);
+              vst(vd + idx, dn);
+              vst(vx + idx, xn);
+              vst(vr + idx, rn);
+              vu[idx] = un;
               l_gam += rn * un;
               l_rr += rn * rn;
               l_uu += un * un;
@@ -654,12 +660,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
         a_uu = (double)l_uu;
         const double v[3] = {a_gam, a_rr, a_uu};
         const int sl[3] = {S_GAM, S_RR, S_UU};
-        block_store<K, 3>(v, sl, P.part, red);
+        block_store<K, 3>(v, sl, P.part, red, bid);
       }
       if (!sync()) return;
       {
         const int sl[3] = {S_GAM, S_RR, S_UU};
-        grid_reduce<K, 3>(sl, P.part, res);
+        grid_reduce<K, 3>(sl, P.part, res, nb);
       }
       ++iters;
       if (threadIdx.x < K) {
@@ -697,7 +703,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
     for (int64_t idx = gtid; idx < NK; idx += gstride)
       P.z_out[(int64_t)(c >> P.col_shift) * P.ld + P.perm[idx / K]] = to_double(P.q[idx]) * isc[c] + mu[c];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (bid == 0 && threadIdx.x == 0) {
     int all_done = 1;
     for (int j = 0; j < K; ++j) all_done &= done[j];
     if (!all_done) atomicOr(status, kErrNotConverged);
@@ -706,27 +712,57 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveParams<VI> P) {
   }
 }
 
+template <typename VI, int K>
+__global__ void __launch_bounds__(kThreads, 2) k_solve(const __grid_constant__ SolveParams<VI> P) {
+  solve_body<VI, K>(P, blockIdx.x, gridDim.x);
+}
+
+// Several independent problems in one cooperative launch (small graphs
+// packed together): problem p runs on blocks [first_block[p],
+// first_block[p + 1]) with its own barrier, reduction slots, workspace and
+// convergence control.
+constexpr int kPackMax = FJ_PACK_MAX;
+template <typename VI>
+struct PackParams {
+  int count;
+  int first_block[kPackMax + 1];
+  SolveParams<VI> prob[kPackMax];
+};
+// kernel parameters are limited to 32764 bytes
+static_assert(sizeof(PackParams<float>) <= 32000 && sizeof(PackParams<double>) <= 32000,
+              "packed launch parameters too large");
+
+template <typename VI, int K>
+__global__ void __launch_bounds__(kThreads, 2) k_solve_packed(const __grid_constant__ PackParams<VI> PP) {
+  int p = 0;  // block-uniform
+  while (p + 1 < PP.count && (int)blockIdx.x >= PP.first_block[p + 1]) ++p;
+  const int b0 = PP.first_block[p];
+  solve_body<VI, K>(PP.prob[p], (int)blockIdx.x - b0, PP.first_block[p + 1] - b0);
+}
+
 // ------------------------------------------------------------------ host
 
 // Limit of every grid-barrier wait, and the test hook's withheld barrier
 // (fj_debug_barrier).
 constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // 4 s
-// Bytes of a walk's gathered vector kept in L2 (of 126 MB): the rows of the
-// highest degree, which most gathers hit, up to this size.
-constexpr int64_t kL2KeepBytes = 80ll << 20;
 std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};
 std::atomic<int> g_withhold{0};
 
+// Dynamic shared memory of the solve kernels (reduction scratch, or the
+// wide walks' staging).
 template <typename VI, int K>
-static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, const double* s,
-                            int64_t ld, double* z, double* quant, double* resid, int* status,
-                            char* ws, size_t ws_bytes, const fj_opts& o, int mode, int max_blocks,
-                            bool paper, const double* z0, int* grid_out) {
-  auto kern = k_solve<VI, K>;
+static size_t solve_dyn_smem() {
   const size_t red_bytes = (size_t)7 * kWarps * K * sizeof(double);
   const size_t stage = (K <= 4) ? 0 : (size_t)kWarps * kWideStageBytes;
-  const size_t dyn = std::max(red_bytes, stage);
-  // the attribute and the occupancy query once per device and instantiation
+  return std::max(red_bytes, stage);
+}
+
+// Co-resident blocks per SM of k_solve<VI, K> and k_solve_packed<VI, K> on
+// the current device (the attribute and the occupancy query once per device
+// and instantiation; the two kernels share the body and its resources, and
+// the smaller of the two counts is returned).
+template <typename VI, int K>
+static fj_status solve_blocks_per_sm(int* out) {
   static std::mutex setup_mu;
   static int per_sm_of[kMaxDevices] = {};
   int device = 0;
@@ -735,36 +771,40 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
     set_error("device %d out of range", device);
     return FJ_ERR_ARG;
   }
-  int per_sm = 0;
-  {
-    std::lock_guard<std::mutex> lock(setup_mu);
-    if (per_sm_of[device] == 0) {
-      FJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-      FJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, dyn));
-      per_sm_of[device] = per_sm > 0 ? per_sm : -1;
-    }
-    per_sm = per_sm_of[device];
+  std::lock_guard<std::mutex> lock(setup_mu);
+  if (per_sm_of[device] == 0) {
+    const size_t dyn = solve_dyn_smem<VI, K>();
+    int a = 0, b = 0;
+    FJ_CUDA(cudaFuncSetAttribute(k_solve<VI, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    FJ_CUDA(cudaFuncSetAttribute(k_solve_packed<VI, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    FJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_solve<VI, K>, kThreads, dyn));
+    FJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_solve_packed<VI, K>, kThreads, dyn));
+    const int per_sm = std::min(std::min(a, b), kMaxBlocksPerSM);
+    per_sm_of[device] = per_sm > 0 ? per_sm : -1;
   }
-  if (per_sm < 1) {
+  if (per_sm_of[device] < 1) {
     set_error("solver kernel does not fit on an SM");
     return FJ_ERR_CUDA;
   }
-  const int64_t n = g->n;
-  // grid: enough blocks for the work, at most what is co-resident
-  // about 16 path items per thread before the grid stops growing; a
-  // negative max_blocks asks for exactly -max_blocks blocks instead
-  const int64_t work = n * K + g->nnz * K;
-  int64_t want = (work + kThreads * 16 - 1) / (kThreads * 16);
-  if (want < 1) want = 1;
-  int64_t cap = (int64_t)std::min(per_sm, kMaxBlocksPerSM) * num_sms;
-  if (max_blocks < 0)
-    want = -(int64_t)max_blocks;
-  else if (max_blocks > 0 && cap > max_blocks)
-    cap = max_blocks;
-  const int blocks = (int)std::min(want, cap);
-  if (grid_out && *grid_out < blocks) *grid_out = blocks;
+  *out = per_sm_of[device];
+  return FJ_OK;
+}
 
-  // carve the workspace
+// Blocks a solve of K columns on g asks for when sized by its work: about 16
+// path items per thread.
+static int64_t work_blocks(const fj_graph* g, int K) {
+  const int64_t work = g->n * K + g->nnz * K;
+  const int64_t want = (work + kThreads * 16 - 1) / (kThreads * 16);
+  return want < 1 ? 1 : want;
+}
+
+// Fills the parameters of one problem (K columns of s on g, on `blocks`
+// blocks) and carves its workspace from ws.
+template <typename VI, int K>
+static fj_status fill_params(SolveParams<VI>& P, const fj_graph* g, const double* s, int64_t ld, double* z,
+                             double* quant, double* resid, int* status, char* ws, size_t ws_bytes,
+                             const fj_opts& o, int mode, int blocks, bool paper, const double* z0) {
+  const int64_t n = g->n;
   const int64_t NK = n * K;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -772,7 +812,6 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
     off += (bytes + 255) & ~size_t(255);
     return (void*)p;
   };
-  SolveParams<VI> P;
   P.sg = SellGraph{g->row_ptr,   g->col,       g->val,      g->long_first, g->chunk_row,
                    g->chunk_begin, g->chunk_end, g->slice_off, g->sell_col,   g->sell_val,
                    g->unit_prefix, n,            g->n_long,   g->n_nz,       g->n_chunks,
@@ -815,12 +854,61 @@ static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, con
   P.z0 = z0;
   P.col_shift = paper ? 1 : 0;
   P.timeout_ns = g_wait_ns.load(std::memory_order_relaxed);
-  P.hot_inner = (int32_t)std::min<int64_t>(n, kL2KeepBytes / ((int64_t)K * (int64_t)sizeof(VI)));
-  P.hot_ref = (int32_t)std::min<int64_t>(n, kL2KeepBytes / ((int64_t)K * 8));
   P.withhold = (unsigned)g_withhold.load(std::memory_order_relaxed);
+  return FJ_OK;
+}
+
+template <typename VI, int K>
+static fj_status launch_one(const fj_graph* g, cudaStream_t st, int num_sms, const double* s,
+                            int64_t ld, double* z, double* quant, double* resid, int* status,
+                            char* ws, size_t ws_bytes, const fj_opts& o, int mode, int max_blocks,
+                            bool paper, const double* z0, int* grid_out) {
+  int per_sm = 0;
+  fj_status rc = solve_blocks_per_sm<VI, K>(&per_sm);
+  if (rc != FJ_OK) return rc;
+  // grid: enough blocks for the work, at most what is co-resident; a
+  // negative max_blocks asks for exactly -max_blocks blocks instead
+  int64_t want = work_blocks(g, K);
+  int64_t cap = (int64_t)per_sm * num_sms;
+  if (max_blocks < 0)
+    want = -(int64_t)max_blocks;
+  else if (max_blocks > 0 && cap > max_blocks)
+    cap = max_blocks;
+  const int blocks = (int)std::min(want, cap);
+  if (grid_out && *grid_out < blocks) *grid_out = blocks;
+  SolveParams<VI> P;
+  rc = fill_params<VI, K>(P, g, s, ld, z, quant, resid, status, ws, ws_bytes, o, mode, blocks, paper, z0);
+  if (rc != FJ_OK) return rc;
   FJ_CUDA(cudaMemsetAsync(P.bar, 0, 64, st));
   void* args[] = {&P};
-  FJ_CUDA(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(kThreads), args, dyn, st));
+  FJ_CUDA(cudaLaunchCooperativeKernel((void*)k_solve<VI, K>, dim3(blocks), dim3(kThreads), args,
+                                      solve_dyn_smem<VI, K>(), st));
+  count_launches(1);
+  return FJ_OK;
+}
+
+// One packed launch of `count` problems of K columns each (PackItem i: graph,
+// its columns, outputs, workspace, blocks).  Every problem's barrier and
+// unit counter sit in `bars` (count x 64 bytes, zeroed here).
+template <typename VI, int K>
+static fj_status launch_packed(int count, const PackItem* it, cudaStream_t st, const fj_opts& o, int mode,
+                               char* bars) {
+  PackParams<VI> PP;
+  PP.count = count;
+  PP.first_block[0] = 0;
+  for (int i = 0; i < count; ++i) {
+    fj_status rc = fill_params<VI, K>(PP.prob[i], it[i].g, it[i].s, it[i].ld, it[i].z, it[i].quant,
+                                      it[i].resid, it[i].status, it[i].ws, it[i].ws_bytes, it[i].opts, mode,
+                                      it[i].blocks, false, nullptr);
+    if (rc != FJ_OK) return rc;
+    PP.prob[i].bar = (Barrier*)(bars + 64 * i);
+    PP.prob[i].unit_counter = (unsigned long long*)(bars + 64 * i + 32);
+    PP.first_block[i + 1] = PP.first_block[i] + it[i].blocks;
+  }
+  FJ_CUDA(cudaMemsetAsync(bars, 0, (size_t)64 * count, st));
+  void* args[] = {&PP};
+  FJ_CUDA(cudaLaunchCooperativeKernel((void*)k_solve_packed<VI, K>, dim3(PP.first_block[count]), dim3(kThreads),
+                                      args, solve_dyn_smem<VI, K>(), st));
   count_launches(1);
   return FJ_OK;
 }
@@ -841,10 +929,10 @@ extern "C" fj_status fj_debug_barrier(int64_t wait_ns, int32_t withhold) {
   return FJ_OK;
 }
 
-// Workspace bytes one launch of K columns needs.
-size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms) {
+// Workspace bytes of one problem of K columns solved on at most `blocks`
+// blocks.
+size_t fj_solve_workspace_bytes_blocks(const fj_graph* g, int K, int inner_bytes, int64_t blocks) {
   const int64_t NK = g->n * (int64_t)K;
-  const int64_t blocks = (int64_t)num_sms * kMaxBlocksPerSM;
   size_t b = 0;
   auto add = [&](size_t x) { b += (x + 255) & ~size_t(255); };
   add(NK * 8);
@@ -857,6 +945,11 @@ size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int n
   add(std::max<int64_t>(g->n_units, 1) * K * 8);
   add(64);
   return b;
+}
+
+// Workspace bytes one launch of K columns needs (on any grid).
+size_t fj_solve_workspace_bytes(const fj_graph* g, int K, int inner_bytes, int num_sms) {
+  return fj_solve_workspace_bytes_blocks(g, K, inner_bytes, (int64_t)num_sms * kMaxBlocksPerSM);
 }
 
 // Runs the solve for columns [0, k) of s (column-major, leading dim n, all
@@ -909,6 +1002,59 @@ fj_status fj_solve_device(const fj_graph* g, cudaStream_t st, int num_sms, int32
   }
   *launches_out = li;
   return FJ_OK;
+}
+
+// Packed solves: blocks a problem of K columns on g takes in a packed launch
+// (sized by its work, at most `cap`), and the blocks one packed launch may
+// use in all (every block co-resident).
+int fj_pack_blocks(const fj_graph* g, int K, int cap) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(work_blocks(g, K), cap));
+}
+
+fj_status fj_pack_capacity(int precision, int K, int num_sms, int* out) {
+  int per_sm = 0;
+  fj_status rc = FJ_OK;
+#define FJ_PER_SM(KK)                                                                     \
+  rc = precision == FJ_PREC_FP64 ? solve_blocks_per_sm<double, KK>(&per_sm)               \
+                                 : solve_blocks_per_sm<float, KK>(&per_sm);
+  switch (K) {
+    case 32: FJ_PER_SM(32) break;
+    case 16: FJ_PER_SM(16) break;
+    case 8: FJ_PER_SM(8) break;
+    case 4: FJ_PER_SM(4) break;
+    case 2: FJ_PER_SM(2) break;
+    default: FJ_PER_SM(1) break;
+  }
+#undef FJ_PER_SM
+  if (rc != FJ_OK) return rc;
+  *out = per_sm * num_sms;
+  return FJ_OK;
+}
+
+// Runs `count` (1 <= count <= FJ_PACK_MAX) problems of K columns each in one
+// cooperative launch on st, in the precision of o (each problem's own
+// tolerances and caps come with its item).  The sum of the items' blocks
+// must not exceed fj_pack_capacity.  bars: device scratch of 64 * count
+// bytes.
+fj_status fj_solve_packed_device(int K, int count, const PackItem* items, cudaStream_t st, const fj_opts& o,
+                                 char* bars) {
+  if (count < 1 || count > kPackMax) {
+    set_error("internal: %d problems in one packed launch (1..%d)", count, kPackMax);
+    return FJ_ERR_ARG;
+  }
+  const int mode = o.precision == FJ_PREC_FP64 ? kModeFP64 : (o.precision == FJ_PREC_FP32 ? kModeFP32 : kModeMixed);
+#define FJ_PACK(KK)                                                                   \
+  return mode == kModeFP64 ? launch_packed<double, KK>(count, items, st, o, mode, bars) \
+                           : launch_packed<float, KK>(count, items, st, o, mode, bars);
+  switch (K) {
+    case 32: FJ_PACK(32)
+    case 16: FJ_PACK(16)
+    case 8: FJ_PACK(8)
+    case 4: FJ_PACK(4)
+    case 2: FJ_PACK(2)
+    default: FJ_PACK(1)
+  }
+#undef FJ_PACK
 }
 
 // ------------------------------------------------- allocation-free solve

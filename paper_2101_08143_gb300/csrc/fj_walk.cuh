@@ -85,53 +85,6 @@ __device__ __forceinline__ void load_k(const T* __restrict__ p, T (&v)[K]) {
   }
 }
 
-// load_k with the cache priority of the gathers: rows of x below the walk's
-// `hot` limit (the highest-degree rows, which most gathers hit) are loaded
-// normally and stay in L2; the other rows are streamed (evict-first).
-template <typename T, int K>
-__device__ __forceinline__ void load_k(const T* __restrict__ p, bool keep, T (&v)[K]) {
-  if (keep) {
-    load_k<T, K>(p, v);
-    return;
-  }
-  if constexpr (std::is_same<T, df64>::value) {
-    if constexpr (K % 2 == 0) {
-#pragma unroll
-      for (int cc = 0; cc < K; cc += 2) {
-        const float4 q = ld_cs(reinterpret_cast<const float4*>(p) + cc / 2);
-        v[cc] = df_make(q.x, q.y);
-        v[cc + 1] = df_make(q.z, q.w);
-      }
-    } else {
-#pragma unroll
-      for (int cc = 0; cc < K; ++cc) {
-        const float2 q = ld_cs(reinterpret_cast<const float2*>(p) + cc);
-        v[cc] = df_make(q.x, q.y);
-      }
-    }
-  } else if constexpr (K * sizeof(T) == 16 && sizeof(T) == 4) {
-    const float4 q = ld_cs(reinterpret_cast<const float4*>(p));
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-  } else if constexpr (K * sizeof(T) == 16 && sizeof(T) == 8) {
-    const double2 q = ld_cs(reinterpret_cast<const double2*>(p));
-    v[0] = q.x; v[1] = q.y;
-  } else if constexpr (K * sizeof(T) == 8 && sizeof(T) == 4) {
-    const float2 q = ld_cs(reinterpret_cast<const float2*>(p));
-    v[0] = q.x; v[1] = q.y;
-  } else {
-#pragma unroll
-    for (int cc = 0; cc < K; ++cc) v[cc] = ld_cs(p + cc);
-  }
-}
-
-// One value of x, kept in L2 or streamed (the wide walks' gathers).
-__device__ __forceinline__ float ld_x(const float* p, bool keep) { return keep ? *p : ld_cs(p); }
-__device__ __forceinline__ double ld_x(const double* p, bool keep) { return keep ? *p : ld_cs(p); }
-__device__ __forceinline__ df64 ld_x(const df64* p, bool keep) {
-  const float2 q = keep ? *reinterpret_cast<const float2*>(p) : ld_cs(reinterpret_cast<const float2*>(p));
-  return df_make(q.x, q.y);
-}
-
 // Streaming store of a walk's row sum (read once, by the next phase).
 __device__ __forceinline__ void st_row(float* p, float v) { st_cs(p, v); }
 __device__ __forceinline__ void st_row(double* p, double v) { st_cs(p, v); }
@@ -157,12 +110,12 @@ __device__ __forceinline__ int64_t sell_unit_start(const SellGraph& g, int64_t w
 
 // out[r*K+c] = sum_j w_rj (x[r*K+c] - x[j*K+c]) for every row of units
 // [u0, u1); quad[c] accumulates this lane's share of sum w (x_r - x_j)^2.
-// The graph and the row sums are streamed (evict-first); the gathers of rows
-// below `hot` are plain loads, so that those rows of x stay in L2.
+// The graph and the row sums are streamed (evict-first) and the gathers of x
+// are plain loads, so that x stays in L2 while the graph streams past it.
 template <typename T, int K, int kB>
 __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
                                           T* __restrict__ part, int64_t u0,
-                                          int64_t u1, T (&quad)[K], int32_t hot) {
+                                          int64_t u1, T (&quad)[K]) {
   const int lane = threadIdx.x & 31;
   // kB: entries in flight per lane between two dependent round trips
   // bounds of unit u: a chunk's row and entry range, or a slice's offsets;
@@ -191,7 +144,7 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
       const int32_t b = (int32_t)lo_cur, e = (int32_t)hi_cur;
       const int32_t nch = g.long_first[r + 1] - g.long_first[r];
       T xr[K], acc[K];
-      load_k<T, K>(x + (int64_t)r * K, true, xr);
+      load_k<T, K>(x + (int64_t)r * K, xr);
 #pragma unroll
       for (int cc = 0; cc < K; ++cc) acc[cc] = num<T>(0.f);
       // batches of kB entries per lane: all index loads, then all gathers
@@ -207,7 +160,7 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
         T xj[kB][K];
 #pragma unroll
         for (int q = 0; q < kB; ++q)
-          load_k<T, K>(x + (int64_t)j[q] * K, j[q] < hot, xj[q]);
+          load_k<T, K>(x + (int64_t)j[q] * K, xj[q]);
 #pragma unroll
         for (int q = 0; q < kB; ++q) {
 #pragma unroll
@@ -238,7 +191,7 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
       const int64_t row = g.n_long + 32 * s + lane;
       if (row < g.n) {
         T xr[K], acc[K];
-        load_k<T, K>(x + row * K, (int32_t)row < hot, xr);
+        load_k<T, K>(x + row * K, xr);
 #pragma unroll
         for (int cc = 0; cc < K; ++cc) acc[cc] = num<T>(0.f);
         const int32_t* __restrict__ cp = g.sell_col + off + lane;
@@ -256,7 +209,7 @@ __device__ __forceinline__ void sell_walk(const SellGraph& g, const T* __restric
           T xj[kB][K];
 #pragma unroll
           for (int q = 0; q < kB; ++q)
-            load_k<T, K>(x + (int64_t)j[q] * K, j[q] < hot, xj[q]);
+            load_k<T, K>(x + (int64_t)j[q] * K, xj[q]);
 #pragma unroll
           for (int q = 0; q < kB; ++q) {
 #pragma unroll
@@ -297,7 +250,7 @@ constexpr int kWideStageBytes = 4096;
 template <typename T, int K>
 __device__ __forceinline__ void wide_unit(const SellGraph& g, const T* __restrict__ x, T* __restrict__ out,
                                           T* __restrict__ part, int64_t u, T& quad,
-                                          T* __restrict__ sxr, int32_t hot) {
+                                          T* __restrict__ sxr) {
   constexpr int SUB = 32 / K;
   constexpr int RB = 32 / SUB;  // rows per sub-group in a slice
   const int lane = threadIdx.x & 31;
@@ -315,13 +268,13 @@ __device__ __forceinline__ void wide_unit(const SellGraph& g, const T* __restric
       for (int t = 0; t < kWB; ++t) {
         const int32_t p = p0 + t * SUB;
         const bool in = p < e;
-        j[t] = in ? ld_ro(g.col + p) : r;
-        w[t] = in ? (g.val ? ld_ro(g.val + p) : 1.0f) : 0.0f;
+        j[t] = in ? g.col[p] : r;
+        w[t] = in ? (g.val ? g.val[p] : 1.0f) : 0.0f;
       }
       T xj[kWB];
 #pragma unroll
       for (int t = 0; t < kWB; ++t)
-        xj[t] = ld_x(x + (int64_t)j[t] * K + c, j[t] < hot);
+        xj[t] = x[(int64_t)j[t] * K + c];
 #pragma unroll
       for (int t = 0; t < kWB; ++t) {
         const T df = xr - xj[t];
@@ -382,13 +335,13 @@ __device__ __forceinline__ void wide_unit(const SellGraph& g, const T* __restric
 #pragma unroll
     for (int t = 0; t < kWB; ++t) {
       const bool in = p + t < pend;
-      j[t] = in ? ld_ro(g.col + p + t) : 0;
-      w[t] = in ? (g.val ? ld_ro(g.val + p + t) : 1.0f) : 0.0f;
+      j[t] = in ? g.col[p + t] : 0;
+      w[t] = in ? (g.val ? g.val[p + t] : 1.0f) : 0.0f;
     }
     T xj[kWB];
 #pragma unroll
     for (int t = 0; t < kWB; ++t)
-      xj[t] = ld_x(x + (int64_t)j[t] * K + c, j[t] < hot);
+      xj[t] = x[(int64_t)j[t] * K + c];
 #pragma unroll
     for (int t = 0; t < kWB; ++t) {
       if (p < pend) {

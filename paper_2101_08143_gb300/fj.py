@@ -56,7 +56,9 @@ class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("device_ms", ctypes.c_double),
                 ("status", ctypes.c_int32), ("columns", ctypes.c_int32),
-                ("blocks", ctypes.c_int32), ("warnings", ctypes.c_uint32)]
+                ("blocks", ctypes.c_int32), ("warnings", ctypes.c_uint32),
+                ("t_begin_ms", ctypes.c_double), ("t_end_ms", ctypes.c_double),
+                ("batched", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -64,6 +66,18 @@ class Info(ctypes.Structure):
 
 class Quant(ctypes.Structure):
     _fields_ = [(name, ctypes.c_double) for name in QUANTITY_NAMES]
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [("chunk_len", ctypes.c_int32), ("sell_max", ctypes.c_int32)]
+
+
+FJ_LAYOUT_TUNE_MAX = 16
+
+
+class LayoutTuneResult(ctypes.Structure):
+    _fields_ = [("best", Layout), ("count", ctypes.c_int32), ("tried", Layout * FJ_LAYOUT_TUNE_MAX),
+                ("ms", ctypes.c_double * FJ_LAYOUT_TUNE_MAX)]
 
 
 class TuneResult(ctypes.Structure):
@@ -110,6 +124,15 @@ _SIGNATURES = {
     "fj_solve_fixed": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, ctypes.POINTER(Opts),
                                         ctypes.POINTER(Info)]),
     "fj_debug_barrier": (ctypes.c_int32, [ctypes.c_int64, ctypes.c_int32]),
+    "fj_graph_update_weights": (ctypes.c_int32, [_P, _P, ctypes.c_int64, _P, _P, _P, ctypes.c_uint32]),
+    "fj_set_layout": (ctypes.c_int32, [_P, ctypes.POINTER(Layout)]),
+    "fj_graph_layout": (ctypes.c_int32, [_P, ctypes.POINTER(Layout)]),
+    "fj_tune_layout": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, ctypes.c_uint32,
+                                        ctypes.c_int32, _P, ctypes.POINTER(Opts), ctypes.c_int32,
+                                        ctypes.POINTER(LayoutTuneResult)]),
+    "fj_serve_pack": (ctypes.c_int32, [_P, ctypes.c_int64]),
+    "fj_solve_batch": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.POINTER(Opts),
+                                        _P]),
 }
 
 _lib = None
@@ -182,6 +205,28 @@ class Graph:
                "fj_graph_node_ids")
         return ids
 
+    def layout(self):
+        lay = Layout()
+        _check(load().fj_graph_layout(self.handle, ctypes.byref(lay)), "fj_graph_layout")
+        return {"chunk_len": lay.chunk_len, "sell_max": lay.sell_max}
+
+    def update_weights(self, src, dst, w):
+        """fj_graph_update_weights: new weights for existing pairs (host
+        numpy arrays, or torch CUDA tensors: int32, int32, float32)."""
+        lib = load()
+        if _is_torch_cuda(src):
+            count = int(src.numel())
+            rc = lib.fj_graph_update_weights(self.ctx.handle, self.handle, count, _P(src.data_ptr()),
+                                             _P(dst.data_ptr()), _P(w.data_ptr()), FJ_DEVICE_PTRS)
+        else:
+            src = np.ascontiguousarray(src, dtype=np.int32)
+            dst = np.ascontiguousarray(dst, dtype=np.int32)
+            w = np.ascontiguousarray(w, dtype=np.float32)
+            rc = lib.fj_graph_update_weights(self.ctx.handle, self.handle, int(src.shape[0]),
+                                             _P(src.ctypes.data), _P(dst.ctypes.data), _P(w.ctypes.data),
+                                             FJ_HOST_PTRS)
+        _check(rc, "fj_graph_update_weights")
+
     def free(self):
         if self.handle:
             _check(load().fj_graph_free(self.ctx.handle, self.handle), "fj_graph_free")
@@ -251,6 +296,57 @@ class Context:
         del keep
         _check(rc, "fj_graph_upload")
         return Graph(self, h)
+
+    def set_layout(self, chunk_len=None, sell_max=None):
+        """Layout of later uploads (None, None: the defaults)."""
+        if chunk_len is None and sell_max is None:
+            _check(load().fj_set_layout(self.handle, None), "fj_set_layout")
+            return
+        lay = Layout(512 if chunk_len is None else chunk_len, 64 if sell_max is None else sell_max)
+        _check(load().fj_set_layout(self.handle, ctypes.byref(lay)), "fj_set_layout")
+
+    def tune_layout(self, n, src, dst, w, s, opts: Opts | None = None, repeats: int = 3,
+                    merge_duplicates=False):
+        """fj_tune_layout on host or device (torch) edge arrays and opinions;
+        returns {"best": (chunk_len, sell_max), "ms": {(chunk_len, sell_max): ms}}."""
+        lib = load()
+        o = Opts()
+        lib.fj_default_opts(ctypes.byref(o))
+        if opts is not None:
+            o = Opts(opts.tol, opts.inner_tol, opts.precision, opts.max_iter, opts.max_refine, opts.flags)
+        keep = []
+        if _is_torch_cuda(src):
+            flags = FJ_DEVICE_PTRS
+            m = int(src.numel())
+            sp, dp = src.data_ptr(), dst.data_ptr()
+            wp = w.data_ptr() if w is not None else None
+        else:
+            flags = FJ_HOST_PTRS
+            src = np.ascontiguousarray(src, dtype=np.int32)
+            dst = np.ascontiguousarray(dst, dtype=np.int32)
+            w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+            keep += [src, dst, w]
+            m = int(src.shape[0])
+            sp, dp = src.ctypes.data, dst.ctypes.data
+            wp = w.ctypes.data if w is not None else None
+        if merge_duplicates:
+            flags |= FJ_MERGE_DUPLICATES
+        if _is_torch_cuda(s):
+            k = 1 if s.dim() == 1 else int(s.shape[0])
+            o.flags = (o.flags & ~FJ_DEVICE_PTRS) | FJ_DEVICE_PTRS
+            s_ptr = s.data_ptr()
+        else:
+            s2 = np.asfortranarray(np.asarray(s, dtype=np.float64).reshape(n, -1))
+            keep.append(s2)
+            k = s2.shape[1]
+            o.flags = o.flags & ~FJ_DEVICE_PTRS
+            s_ptr = s2.ctypes.data
+        res = LayoutTuneResult()
+        _check(lib.fj_tune_layout(self.handle, int(n), m, _P(sp), _P(dp), _P(wp), flags, k, _P(s_ptr),
+                                  ctypes.byref(o), int(repeats), ctypes.byref(res)), "fj_tune_layout")
+        del keep
+        return {"best": (res.best.chunk_len, res.best.sell_max),
+                "ms": {(res.tried[i].chunk_len, res.tried[i].sell_max): res.ms[i] for i in range(res.count)}}
 
     def upload_edges(self, edges, merge_duplicates=False) -> Graph:
         """Upload a synth.EdgeList."""
@@ -332,6 +428,60 @@ class Context:
         d["rc"] = rc
         return z, qs, d
 
+    def solve_batch(self, graphs, s_list, want_z=True, opts: Opts | None = None, raise_on_error=True):
+        """fj_solve_batch: many problems in packed launches.
+
+        graphs: list of Graph; s_list: per problem a host numpy float64 (n,)
+        or (n, k) array, or (all of them) torch float64 CUDA tensors of shape
+        (k, n) / (n,).  Returns (rc, [(z, quantities, info) per problem])."""
+        lib = load()
+        o = Opts()
+        lib.fj_default_opts(ctypes.byref(o))
+        if opts is not None:
+            o = Opts(opts.tol, opts.inner_tol, opts.precision, opts.max_iter, opts.max_refine, opts.flags)
+        count = len(graphs)
+        device = _is_torch_cuda(s_list[0])
+        ks, sp, zp, zs, keep = [], [], [], [], []
+        for g, sv in zip(graphs, s_list):
+            n = g.stats()["n"]
+            if device:
+                k = 1 if sv.dim() == 1 else int(sv.shape[0])
+                if not sv.is_contiguous() or sv.numel() != n * k:
+                    raise ValueError("device s must be contiguous float64 with n*k elements")
+                z = None
+                if want_z:
+                    import torch
+                    z = torch.empty_like(sv)
+                sp.append(sv.data_ptr())
+                zp.append(z.data_ptr() if z is not None else None)
+            else:
+                s2 = np.asfortranarray(np.asarray(sv, dtype=np.float64).reshape(n, -1))
+                k = s2.shape[1]
+                z = np.empty((n, k), dtype=np.float64, order="F") if want_z else None
+                keep.append(s2)
+                sp.append(s2.ctypes.data)
+                zp.append(z.ctypes.data if z is not None else None)
+            ks.append(k)
+            zs.append(z)
+        o.flags = (o.flags & ~FJ_DEVICE_PTRS) | (FJ_DEVICE_PTRS if device else FJ_HOST_PTRS)
+        quants = [(Quant * k)() for k in ks]
+        infos = (Info * count)()
+        ga = (_P * count)(*[g.handle for g in graphs])
+        ka = (ctypes.c_int32 * count)(*ks)
+        sa = (_P * count)(*sp)
+        za = (_P * count)(*zp) if want_z else None
+        qa = (_P * count)(*[ctypes.cast(q, _P) for q in quants])
+        rc = lib.fj_solve_batch(self.handle, count, ga, ka, sa, za, qa, ctypes.byref(o), infos)
+        del keep
+        if raise_on_error and rc != FJ_OK:
+            _check(rc, "fj_solve_batch")
+        out = []
+        for i in range(count):
+            qs = [{name: getattr(quants[i][j], name) for name in QUANTITY_NAMES} for j in range(ks[i])]
+            d = infos[i].as_dict()
+            out.append((zs[i], qs, d))
+        return rc, out
+
     def quantities(self, graph: Graph, s, opts: Opts | None = None):
         _, q, info = self.solve(graph, s, want_z=False, want_quant=True, opts=opts)
         return q, info
@@ -395,6 +545,12 @@ def _serve_opts(opts):
 def serve_config(ctx: "Context", max_inflight=0, mem_budget_bytes=0, max_blocks_per_request=-1):
     _check(load().fj_serve_config(ctx.handle, int(max_inflight), int(mem_budget_bytes),
                                   int(max_blocks_per_request)), "fj_serve_config")
+
+
+def serve_pack(ctx: "Context", max_nodes: int):
+    """Requests with at most max_nodes nodes are solved in packed batches
+    (0: none)."""
+    _check(load().fj_serve_pack(ctx.handle, int(max_nodes)), "fj_serve_pack")
 
 
 def submit(ctx: "Context", graph: "Graph", s, opts: Opts | None = None) -> Ticket:

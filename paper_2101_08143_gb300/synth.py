@@ -222,6 +222,10 @@ WORKLOADS = {
     "cl_n20m_m150m_b2.1": dict(kind="cl", n=20_000_000, m=150_000_000,
                                exponent=2.1, weighted=True, k=1,
                                opinions="uniform", seed=5),
+    # the 20M/150M shape scaled down five-fold (profiling captures)
+    "cl_n4m_m30m_b2.1": dict(kind="cl", n=4_000_000, m=30_000_000,
+                             exponent=2.1, weighted=True, k=1,
+                             opinions="uniform", seed=6),
 }
 
 

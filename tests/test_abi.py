@@ -99,8 +99,10 @@ def test_tune_layout_and_null_arguments_without_a_device():
 
 def test_info_layout_and_set_grid_arguments_without_a_device():
     import ctypes as C
-    # int32 x2, double x2, int32 status, columns, blocks, uint32 warnings
-    assert fj.Info.blocks.offset == 32 and fj.Info.warnings.offset == 36 and C.sizeof(fj.Info) == 40
+    # int32 x2, double x2, int32 status, columns, blocks, uint32 warnings,
+    # double t_begin_ms, t_end_ms, int32 batched, reserved
+    assert fj.Info.blocks.offset == 32 and fj.Info.warnings.offset == 36
+    assert fj.Info.t_begin_ms.offset == 40 and fj.Info.batched.offset == 56 and C.sizeof(fj.Info) == 64
     text = open(os.path.join(ROOT, "include", "fj.h")).read()
     assert int(re.search(r"#define FJ_WARN_OPINION_RANGE (\d+)u", text).group(1)) == fj.FJ_WARN_OPINION_RANGE
     lib = fj.load()

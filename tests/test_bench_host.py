@@ -75,3 +75,30 @@ def test_clock_samples_fall_back_to_the_whole_run(tmp_path):
     out = _sampler(tmp_path, rows, now, now + 1).stop()
     assert out["window"] == "whole run" and out["samples"] == 2
     assert out["reasons"] == ["sw_power_cap"]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_quantity_error_bound_holds(seed):
+    """The certified sigma bound from a residual: perturb the exact solution,
+    and the true relative error of every quantity stays below the bound
+    computed from ||s - (I + L) z|| alone (and the bound is not vacuous)."""
+    import numpy as np
+    import oracle.fj_oracle as fo
+    from paper_2101_08143_gb300 import synth
+    g = synth.chung_lu(300, 1200, 2.3, seed=seed, weighted=True)
+    s = synth.opinions_uniform(g.n, 1, seed)[:, 0]
+    z_star = fo.solve_dense(g.n, g.src, g.dst, g.w, s)
+    q_star = fo.quantities_from_z(g.n, g.src, g.dst, g.w, s, z_star)
+    rng = np.random.default_rng(seed)
+    for scale in (1e-9, 1e-6, 1e-4):
+        z = z_star + scale * rng.standard_normal(g.n)
+        r = s - fo.apply_i_plus_l(g.n, g.src, g.dst, g.w, z)
+        eps = float(np.linalg.norm(r))
+        q_def = fo.quantities_from_z(g.n, g.src, g.dst, g.w, s, z)
+        # a device reduction that is off by a relative 1e-12
+        q_gpu = {k: v * (1 + 1e-12) for k, v in q_def.items()}
+        bound = bench.quantity_error_bound(q_gpu, q_def, eps)
+        for name in fo.QUANTITY_NAMES:
+            true_err = abs(q_gpu[name] - q_star[name]) / q_star[name]
+            assert true_err <= bound[name], (name, scale, true_err, bound[name])
+            assert bound[name] < 1.0
