@@ -3,10 +3,14 @@
 One step = the whole path on one synthetic problem already resident in HBM:
 graph ingest (edge list -> CSR of I + L), centring, the mixed-precision
 Jacobi-PCG solve of (I + L) q = s_bar to the workload's relative residual,
-and the five quantities plus z.  Default workload: Chung-Lu power-law graph,
-n = 1,000,000, m = 5,000,000 undirected edges, exponent 2.3, weights
-Uniform(0,1] float32, one opinion vector s ~ Uniform[0,1], float32 inner
-iterations with float64 refinement to relative residual 1e-8.
+and the five quantities plus z.  Default (headline) workload: Chung-Lu
+power-law graph, n = 20,000,000, m = 150,000,000 undirected edges, exponent
+2.1, weights Uniform(0,1] float32, one opinion vector s ~ Uniform[0,1],
+float32 inner iterations with double-float refinement to relative residual
+1e-8.  The same run times, as sub-records, the same graph with 32 opinion
+vectors, the Chung-Lu 4M/40M graph with 256 vectors, the Chung-Lu 1M/5M
+graph, the Erdos-Renyi 2K graph, and a Poisson serving stream; it states the
+error of every quantity against the float64 oracle.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on the same workload instead.
@@ -32,8 +36,18 @@ sys.path.insert(0, ROOT)
 from paper_2101_08143_gb300 import synth  # noqa: E402
 
 METRIC = "solves/s and HBM GB/s (% of peak) of (I+L)z=s at 1e-6 rel err; p50/p99 latency"
-WORKLOAD = "cl_n1m_m5m_b2.3"
+WORKLOAD = "cl_n20m_m150m_b2.1"
 TOL = 1e-8
+# Sub-records of the default run: (workload, opinion vectors, timed steps).
+SUB_WORKLOADS = (("cl_n20m_m150m_b2.1", 32, 3), ("cl_n4m_m40m_b2.1_k256", 256, 2),
+                 ("cl_n1m_m5m_b2.3", 1, 10))
+# Iterations of the oracle's float64 Jacobi-PCG to relative residual 1e-8 on
+# the workloads too large for its full solve in a few seconds, from a full run
+# of the oracle on the same seeded input (20 iterations, final relative
+# residual 7.5e-9, 258 s on one x86 core); the CPU figures there time a
+# bounded sample (one operator application and the five definitions) and
+# scale it by this count.  Other workloads time the oracle's full solve.
+ORACLE_ITERS = {"cl_n20m_m150m_b2.1": 20}
 # The generated graphs are simple, so uploads pass FJ_MERGE_DUPLICATES and skip
 # the check for repeated pairs.
 MERGE = True
@@ -342,140 +356,424 @@ def small_graph_run(ctx, fj, torch, stream, reps=200):
     return out
 
 
-def serving_run(ctx, fj, n_requests=240, seed=4, rate_fracs=(0.5, 0.8)):
-    """A Poisson stream of requests that bring their own graph (Erdos-Renyi or
-    Chung-Lu, n log-uniform in [10^3, 10^5], average degree U[4, 20],
-    weights U(0,1], 1-16 opinion vectors) through fj_submit_edges / fj_poll.
-    First the saturation throughput (all requests at once), then open loops
-    at each of rate_fracs of it; latency = submit to completion.  The generated
-    graphs are simple, so requests pass FJ_MERGE_DUPLICATES.  All requests
-    are prepared before the clock starts; submitting one still copies its
-    edge list and opinions (the API copies inputs at the call)."""
+def serving_run(ctx, fj, n_requests=10_000, pool_size=48, seed=4, rate_fracs=(0.5, 0.8), window=64,
+                submitters=4, open_loop_s=30.0):
+    """The serving workload: a stream of solve requests that each bring their
+    own graph (Erdos-Renyi or Chung-Lu with exponent U[2.1, 2.5], n
+    log-uniform in [10^3, 10^6], average degree U[4, 20], weights U(0,1],
+    1-16 opinion vectors U[0,1]) through fj_submit_edges / fj_poll.  The
+    graphs come from a pool of `pool_size` drawn from that distribution (every
+    request still uploads its edge list, which the library ingests afresh).
+    First the saturation throughput: `n_requests` requests with `window`
+    outstanding at a time; then open loops with Poisson arrivals at each of
+    rate_fracs of saturation, each `n_requests` long or `open_loop_s` seconds
+    of arrivals, whichever is shorter; latency = submit to completion.  The
+    generated graphs are simple, so requests pass FJ_MERGE_DUPLICATES.  Inputs
+    are prepared before the clock starts; submitting copies them (the API
+    copies inputs at the call)."""
     import threading
     rng = np.random.default_rng(seed)
     pool = []
-    for i in range(24):
-        n = int(10 ** rng.uniform(3, 5))
-        m = int(n * rng.uniform(4, 20) / 2)
+    for i in range(pool_size):
+        n = int(10 ** rng.uniform(3, 6))
+        m = max(1, int(n * rng.uniform(4, 20) / 2))
         if rng.random() < 0.5:
-            gg = synth.erdos_renyi(n, m, seed=seed * 100 + i, weighted=True)
+            gg = synth.erdos_renyi(n, m, seed=seed * 1000 + i, weighted=True)
         else:
-            gg = synth.chung_lu(n, m, rng.uniform(2.1, 2.5), seed=seed * 100 + i, weighted=True)
-        pool.append(gg)
-    reqs = []
-    for r in range(n_requests):
-        gg = pool[int(rng.integers(0, len(pool)))]
-        k = int(rng.integers(1, 17))
-        # s in the API's layout (n x k column-major), so that submitting
-        # copies it once and converts nothing
-        reqs.append((gg, rng.random((k, gg.n)).T))
+            gg = synth.chung_lu(n, m, rng.uniform(2.1, 2.5), seed=seed * 1000 + i, weighted=True)
+        # opinions for up to 16 vectors, column-major: the first k columns of
+        # this array are the n x k column-major input of a k-vector request
+        pool.append((gg, np.asfortranarray(rng.random((16, n)).T)))
+    order = [(int(rng.integers(0, pool_size)), int(rng.integers(1, 17))) for _ in range(n_requests)]
 
-    def run(gaps):
-        t_sub, t_done = [0.0] * len(reqs), [0.0] * len(reqs)
-        tickets = [None] * len(reqs)
-        ready = threading.Semaphore(0)
+    def submit(i):
+        gg, sv = pool[order[i][0]]
+        k = order[i][1]
+        return fj.submit_edges(ctx, gg.n, gg.src, gg.dst, gg.w, sv[:, :k], merge_duplicates=MERGE)
+
+    def run(count, arrivals=None):
+        """Submits requests 0..count-1 (at the given arrival times, or keeping
+        `window` outstanding) from `submitters` threads; returns the latency
+        of each request in ms and the span of the run in s."""
+        t_sub = np.zeros(count)
+        t_done = np.zeros(count)
+        tickets = [None] * count
+        lock = threading.Lock()
+        slots = threading.Semaphore(window if arrivals is None else count)
+        outstanding = []
+        finished = threading.Event()
+        t0 = time.perf_counter()
+
+        def submitter(j):
+            for i in range(j, count, submitters):
+                if arrivals is not None:
+                    target = t0 + arrivals[i]
+                    while True:
+                        dt = target - time.perf_counter()
+                        if dt <= 0:
+                            break
+                        time.sleep(min(dt, 0.0005))
+                slots.acquire()
+                t = time.perf_counter()
+                tk = submit(i)
+                with lock:
+                    t_sub[i] = t
+                    tickets[i] = tk
+                    outstanding.append(i)
 
         def poller():
-            for i in range(len(reqs)):
-                ready.acquire()
-                rc, _, _ = fj.poll(ctx, tickets[i], -1)
-                t_done[i] = time.perf_counter()
-                assert rc == fj.FJ_OK
+            done = 0
+            while done < count:
+                with lock:
+                    cur = list(outstanding)
+                hit = False
+                for i in cur:
+                    rc, _, _ = fj.poll(ctx, tickets[i], 0)
+                    if rc == fj.FJ_PENDING:
+                        continue
+                    assert rc == fj.FJ_OK, rc
+                    t_done[i] = time.perf_counter()
+                    with lock:
+                        outstanding.remove(i)
+                    slots.release()
+                    done += 1
+                    hit = True
+                if not hit:
+                    time.sleep(0.0001)
+            finished.set()
 
-        th = threading.Thread(target=poller)
-        th.start()
-        t0 = time.perf_counter()
-        for i, (gg, sv) in enumerate(reqs):
-            if gaps is not None:
-                target = t0 + gaps[i]
-                while time.perf_counter() < target:
-                    time.sleep(max(0.0, min(0.001, target - time.perf_counter())))
-            t_sub[i] = time.perf_counter()
-            tickets[i] = fj.submit_edges(ctx, gg.n, gg.src, gg.dst, gg.w, sv, merge_duplicates=MERGE)
-            ready.release()
-        th.join()
-        lat = 1000.0 * (np.array(t_done) - np.array(t_sub))
-        span = max(t_done) - t0
-        cols = sum(sv.shape[1] for _, sv in reqs)
-        return lat, span, cols
+        ths = [threading.Thread(target=submitter, args=(j,)) for j in range(submitters)]
+        pt = threading.Thread(target=poller)
+        pt.start()
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        pt.join()
+        return 1000.0 * (t_done - t_sub), float(t_done.max() - t0)
 
-    run(None)  # warm-up
-    lat, span, cols = run(None)
-    sat = len(reqs) / span
+    run(min(200, n_requests))  # warm-up
+    lat, span = run(n_requests)
+    sat = n_requests / span
+    cols = sum(k for _, k in order)
     loops = {}
     for frac in rate_fracs:
-        arrivals = np.cumsum(rng.exponential(1.0 / (frac * sat), len(reqs)))
-        lat2, _, _ = run(arrivals)
-        loops[f"{frac:g}"] = {"rate_per_s": frac * sat,
+        rate = frac * sat
+        count = int(min(n_requests, max(200, rate * open_loop_s)))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
+        lat2, span2 = run(count, arrivals)
+        loops[f"{frac:g}"] = {"rate_per_s": rate, "requests": count, "span_s": span2,
                               "latency_ms": {"p50": float(np.percentile(lat2, 50)),
                                              "p99": float(np.percentile(lat2, 99))}}
-    first = loops[f"{rate_fracs[0]:g}"]
-    return {"requests": len(reqs), "graph_pool": len(pool),
-            "saturation_requests_per_s": sat, "saturation_column_solves_per_s": cols / span,
+    first = loops[f"{rate_fracs[0]:g}"] if rate_fracs else {"rate_per_s": None, "latency_ms": None}
+    ns = np.array([pool[i][0].n for i, _ in order])
+    return {"requests": n_requests, "graph_pool": pool_size, "packed_below_nodes": 1 << 17,
+            "n_range": [int(ns.min()), int(ns.max())], "mean_n": float(ns.mean()),
+            "saturation": {"requests_per_s": sat, "column_solves_per_s": cols / span, "window": window,
+                           "span_s": span, "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                                          "p99": float(np.percentile(lat, 99))}},
             "open_loop_rate_per_s": first["rate_per_s"], "latency_ms": first["latency_ms"],
-            "open_loops_by_fraction_of_saturation": loops,
-            "saturated_latency_ms": {"p50": float(np.percentile(lat, 50)),
-                                     "p99": float(np.percentile(lat, 99))}}
+            "open_loops_by_fraction_of_saturation": loops}
 
 
-def run_cpu_baseline(g, s, n_solves, tol=TOL):
+def batch_run(ctx, fj, torch, stream, count=64, seed=8, reps=3):
+    """Many small graphs (Erdos-Renyi or Chung-Lu, n log-uniform in
+    [10^3, 10^5], average degree U[4, 20], weights U(0,1], 1-16 opinion
+    vectors) solved by one fj_solve_batch call (parts of equal width packed
+    into shared persistent launches) against one fj_solve_ex call per
+    graph.  Graphs and opinions are resident on the device; rates count
+    opinion vectors."""
+    rng = np.random.default_rng(seed)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    graphs, s_list, cols = [], [], 0
+    with torch.cuda.stream(stream):
+        for i in range(count):
+            n = int(10 ** rng.uniform(3, 5))
+            m = max(1, int(n * rng.uniform(4, 20) / 2))
+            if rng.random() < 0.5:
+                gg = synth.erdos_renyi(n, m, seed=seed * 1000 + i, weighted=True)
+            else:
+                gg = synth.chung_lu(n, m, rng.uniform(2.1, 2.5), seed=seed * 1000 + i, weighted=True)
+            k = int(rng.integers(1, 17))
+            graphs.append(ctx.upload_edges(gg, merge_duplicates=MERGE))
+            s_list.append(torch.from_numpy(rng.random((k, n))).to(dev))
+            cols += k
+        o = fj.default_opts(tol=TOL)
+        out = {}
+        for name in ("packed", "one_call_per_graph"):
+            ms = []
+            for r in range(reps + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if name == "packed":
+                    rc, _ = ctx.solve_batch(graphs, s_list, want_z=False, opts=o)
+                    assert rc == fj.FJ_OK
+                else:
+                    for gr, sv in zip(graphs, s_list):
+                        ctx.solve(gr, sv, want_z=False, opts=o)
+                torch.cuda.synchronize()
+                if r > 0:
+                    ms.append(1000.0 * (time.perf_counter() - t0))
+            out[name] = {"ms_per_call": float(np.median(ms)),
+                         "column_solves_per_s": cols * 1000.0 / float(np.median(ms))}
+        for gr in graphs:
+            gr.free()
+    out.update({"graphs": count, "columns": cols,
+                "note": "wall time of the API calls, graphs and opinions resident on the device"})
+    return out
+
+
+def quantity_error_bound(q_gpu, q_def, eps):
+    """Upper bound of each quantity's relative error against the exact
+    solution, from a computed z and its float64 residual r = s - (I + L) z.
+
+    Since I + L has no eigenvalue below 1, e = z - z* = (I + L)^-1 r has
+    ||e|| <= ||r|| = eps, and ||W^1/2 B e||^2 = e^T L e <= r^T (I + L)^-1 r <=
+    eps^2.  Each quantity is ||a||^2 for a vector a that moves with z by one
+    of e, the centred e, or W^1/2 B e (Sec. 3.2 definitions, Lemma PropA), so
+    | ||a||^2 - ||a*||^2 | <= eps (2 ||a|| + eps).  I_dc = D + C adds the two
+    bounds.  q_def holds the definitions evaluated on the computed z (so
+    ||a|| = sqrt(q_def)); q_gpu the values the device reduced, whose distance
+    to q_def is added.  Returns {name: bound on |q_gpu - q*| / q*}."""
+    out = {}
+    dev = {}
+    for name in ("C_I", "D", "P", "C"):
+        dev[name] = eps * (2.0 * np.sqrt(max(q_def[name], 0.0)) + eps)
+    dev["I_dc"] = dev["D"] + dev["C"]
+    for name in ("C_I", "D", "P", "C", "I_dc"):
+        exact_low = q_def[name] - dev[name]
+        err = abs(q_gpu[name] - q_def[name]) + dev[name]
+        out[name] = err / exact_low if exact_low > 0 else float("inf")
+    return out
+
+
+def accuracy_direct(g, s, q_gpu):
+    """sigma = |rho - rho~| / rho (Sec. 5) of each quantity against the
+    oracle's own float64 solve (to relative residual 1e-12)."""
     import oracle.fj_oracle as fo
+    qo = fo.quantities(g.n, g.src, g.dst, g.w, s)[0]
+    return {name: fo.relative_error(qo[name], q_gpu[name]) for name in fo.QUANTITY_NAMES}
+
+
+def accuracy_bound(g, s, z, q_gpu):
+    """Certified bound of sigma for a workload too large for the oracle's
+    full solve: the oracle's float64 residual of the GPU's z and its
+    definitions on that z (quantity_error_bound)."""
+    import oracle.fj_oracle as fo
+    r = s - fo.apply_i_plus_l(g.n, g.src, g.dst, g.w, z)
+    eps = float(np.sqrt(np.dot(r, r)))
+    q_def = fo.quantities_from_z(g.n, g.src, g.dst, g.w, s, z)
+    sbar = s - s.mean()
+    return {"sigma_bound": quantity_error_bound(q_gpu, q_def, eps),
+            "residual_norm": eps, "rel_residual_fp64": eps / float(np.sqrt(np.dot(sbar, sbar))),
+            "device_vs_definitions": {k: abs(q_gpu[k] - q_def[k]) / abs(q_def[k]) for k in q_def}}
+
+
+def cpu_sample(name, g, s):
+    """The float64 oracle on the host cores.  Where its full solve fits in a
+    few seconds the sample is that solve plus the five definitions; on the
+    larger graphs it is one application of I + L (the unit of its CG
+    iteration) and the five definitions, scaled to a full solve of
+    ORACLE_ITERS[name] iterations (+ 2 applications for its setup and final
+    residual).  Returns (solves/s, description, seconds of CPU work)."""
+    import oracle.fj_oracle as fo
+    its = ORACLE_ITERS.get(name)
+    if its is None:
+        t0 = time.perf_counter()
+        fo.quantities(g.n, g.src, g.dst, g.w, s, tol=TOL)
+        dt = time.perf_counter() - t0
+        return 1.0 / dt, f"1 full oracle solve (FP64 Jacobi-PCG to {TOL:g}) + the 5 definitions", dt
     t0 = time.perf_counter()
-    for _ in range(n_solves):
-        fo.quantities(g.n, g.src, g.dst, g.w, s, tol=tol)
-    dt = time.perf_counter() - t0
-    return n_solves / dt, dt
+    fo.apply_i_plus_l(g.n, g.src, g.dst, g.w, s)
+    t_apply = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    fo.quantities_from_z(g.n, g.src, g.dst, g.w, s, s)
+    t_def = time.perf_counter() - t0
+    per_solve = (its + 2) * t_apply + t_def
+    desc = (f"1 oracle application of I+L ({t_apply:.1f} s) and the 5 definitions ({t_def:.1f} s) on the "
+            f"full graph, scaled to the oracle's {its} FP64 Jacobi-PCG iterations to {TOL:g} "
+            f"(+2 applications for setup and final residual): {per_solve:.1f} s per solve")
+    return 1.0 / per_solve, desc, t_apply + t_def
+
+
+def _host_info():
+    cpu = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "processor\t: 0")) and ":" in line:
+                    if line.lower().startswith("model name"):
+                        cpu = line.split(":", 1)[1].strip()
+                        break
+    except OSError:
+        pass
+    if cpu == "unknown":
+        import platform
+        cpu = platform.processor() or platform.machine()
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    cpu = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"cpu_model": cpu, "nproc": os.cpu_count()}
 
 
 def run_reference(args):
-    """The oracle, as it stands, on the arm's workload (host cores)."""
+    """The oracle, as it stands, on the arm's workload (host cores); each step
+    is the bounded sample of cpu_sample."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle.fj_oracle as fo
     spec = synth.WORKLOADS[args.workload]
     g = synth.make_graph(spec)
+    k = spec["k"] if args.k is None else args.k
     s = synth.make_opinions(spec, g.n)[:, 0]
+    nnz = 2 * int(np.count_nonzero(g.src != g.dst))
     for _ in range(args.warmup):  # warm-up: one operator application each
         fo.apply_i_plus_l(g.n, g.src, g.dst, g.w, s)
-    # one step = one full oracle solve + quantities; the run stops early once
-    # REF_BUDGET_S of timed work is done, so that any --steps ends within a
-    # few minutes (the line says how many steps were timed)
-    times = []
+    # the run stops early once REF_BUDGET_S of timed work is done, so that
+    # any --steps ends within a few minutes (the line says how many steps
+    # were timed)
+    rates, times, desc = [], [], ""
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        fo.quantities(g.n, g.src, g.dst, g.w, s, tol=TOL)
-        times.append(time.perf_counter() - t0)
+        v, desc, dt = cpu_sample(args.workload, g, s)
+        rates.append(v)
+        times.append(dt)
         if sum(times) >= REF_BUDGET_S:
             break
-    total = sum(times)
-    value = len(times) / total
+    value = float(np.median(rates))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": len(times), "steps_requested": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _workload_desc(spec, g, 1),
-            "latency_ms": {"p50": 1000 * float(np.percentile(times, 50)),
-                           "p99": 1000 * float(np.percentile(times, 99))},
+            "config": _workload_desc(spec, g, k, nnz),
+            "latency_ms": {"p50": 1000.0 / float(np.percentile(rates, 50)),
+                           "p99": 1000.0 / float(np.percentile(rates, 1))},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} full oracle solves + quantities of the workload "
-                                       f"({total:.1f} s; at most {REF_BUDGET_S:.0f} s of timed work)"},
+                             "sample": f"per step: {desc}; {len(times)} steps, {sum(times):.1f} s of timed "
+                                       f"CPU work (at most {REF_BUDGET_S:.0f} s)", **_host_info()},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+def step_run(ctx, fj, torch, g, s_d, z_d, k, steps, warmup, flush, stream):
+    """Times `steps` steps (upload + solve + quantities + z) of one workload
+    after `warmup`; returns per-step ms, the infos, and the graph's nnz."""
+    dev = s_d.device
+    src_d = torch.from_numpy(g.src).to(dev)
+    dst_d = torch.from_numpy(g.dst).to(dev)
+    w_d = torch.from_numpy(g.w).to(dev) if g.w is not None else None
+    opts = fj.default_opts(tol=TOL, precision=fj.PREC_MIXED)
+
+    def step():
+        gr = ctx.upload(g.n, src_d, dst_d, w_d, merge_duplicates=MERGE)
+        _, q, info = ctx.solve(gr, s_d, opts=opts, z_out=z_d)
+        gr.free()
+        return q, info
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+        gr = ctx.upload(g.n, src_d, dst_d, w_d, merge_duplicates=MERGE)
+        nnz = gr.stats()["nnz"]
+        gr.free()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    infos, qs = [], None
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            qs, info = step()
+            evs[i][1].record(stream)
+            infos.append(info)
+    torch.cuda.synchronize()
+    del src_d, dst_d, w_d
+    return [a.elapsed_time(b) for a, b in evs], infos, nnz, qs
+
+
+def roofline(g, nnz, k, infos, peak):
+    """Algorithmic bytes of the solve launches per step over their measured
+    device time, against the measured HBM copy peak."""
+    kern_ms = float(np.mean([i["device_ms"] for i in infos]))
+    iters = int(round(np.mean([i["iterations"] for i in infos])))
+    refines = int(round(np.mean([i["refinements"] for i in infos])))
+    weighted = g.w is not None
+    # iterations are the maximum over launches (k > 32), so for several
+    # launches the byte count is an upper bound
+    algo = sum(_bytes_per_launch(g.n, nnz, weighted, K, iters, refines) for K in _launch_widths(k))
+    achieved = algo / (kern_ms / 1000.0) / 1e9
+    widths = _launch_widths(k)
+    name = f"k_solve<float,{widths[0]}>" + (f" x {len(widths)} launches" if len(widths) > 1 else "")
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "algorithmic_bytes": algo, "kernel_ms": kern_ms,
+            "iterations": iters, "refinements": refines}
+
+
+def tune_layout(ctx, fj, torch, g, s_d, stream, repeats=3):
+    """fj_tune_layout on the workload's graph (device edge arrays) with up to
+    32 of its opinion vectors; the best layout becomes the context's for the
+    timed steps.  Returns the tuner's table (median solve ms by layout)."""
+    dev = s_d.device
+    src_d = torch.from_numpy(g.src).to(dev)
+    dst_d = torch.from_numpy(g.dst).to(dev)
+    w_d = torch.from_numpy(g.w).to(dev) if g.w is not None else None
+    s_t = s_d[:32].contiguous() if s_d.dim() == 2 else s_d
+    with torch.cuda.stream(stream):
+        res = ctx.tune_layout(g.n, src_d, dst_d, w_d, s_t, opts=fj.default_opts(tol=TOL), repeats=repeats,
+                              merge_duplicates=MERGE)
+    torch.cuda.synchronize()
+    ms = {f"{c}/{m}": v for (c, m), v in res["ms"].items()}
+    return {"best": {"chunk_len": res["best"][0], "sell_max": res["best"][1]},
+            "default_ms": res["ms"][(512, 64)], "best_ms": res["ms"][res["best"]],
+            "gain": res["ms"][(512, 64)] / res["ms"][res["best"]], "solve_ms_by_layout": ms,
+            "columns": int(s_t.shape[0]) if s_t.dim() == 2 else 1}
+
+
+def sub_workload(ctx, fj, torch, name, k, steps, peak, flush, stream, g=None):
+    """One sub-record: the layout tuned on the workload (fj_tune_layout),
+    then `steps` timed steps of workload `name` with k opinion vectors after
+    one warm-up step."""
+    spec = synth.WORKLOADS[name]
+    if g is None:
+        g = synth.make_graph(spec)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s_host = synth.make_opinions(spec, g.n, k)
+    s_d = torch.from_numpy(np.ascontiguousarray(s_host.T)).to(dev)
+    z_d = torch.empty_like(s_d)
+    lay = tune_layout(ctx, fj, torch, g, s_d, stream, repeats=1 if k > 1 else 3)
+    ms, infos, nnz, qs = step_run(ctx, fj, torch, g, s_d, z_d, k, steps, 1, flush, stream)
+    ctx.set_layout()
+    rl = roofline(g, nnz, k, infos, peak)
+    del s_d, z_d
+    torch.cuda.empty_cache()
+    return {"config": _workload_desc(spec, g, k, nnz), "steps": steps,
+            "column_solves_per_s": k * 1000.0 * steps / float(sum(ms)), "ms_per_step": float(np.mean(ms)),
+            "rel_residual": max(i["rel_residual"] for i in infos),
+            "edge_iterations_per_s": nnz * k * rl["iterations"] / (rl["kernel_ms"] / 1000.0),
+            "roofline": rl, "layout": lay, "quantities": qs[0]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--cpu-solves", type=int, default=3, help="oracle solves in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--no-side", action="store_true",
+                    help="time the workload's steps only (no sub-records or side measurements)")
+    ap.add_argument("--serving-requests", type=int, default=10_000)
+    ap.add_argument("--default-layout", action="store_true",
+                    help="skip the layout autotuner (default chunk length and sliced-ELL limit)")
     ap.add_argument("--k", type=int, default=None,
                     help="opinion vectors per step (default: the workload's own)")
     args = ap.parse_args()
@@ -502,10 +800,8 @@ def main():
 
     lib = fj.load()
     spec = synth.WORKLOADS[args.workload]
-    # the side measurements (precision modes, warm start, LCC, serving, CPU
-    # oracle) run on the default workload only; the larger workloads time
-    # the step alone
-    full = args.workload == WORKLOAD and args.k is None
+    # the side measurements run on the default workload at N = 1 only
+    full = args.workload == WORKLOAD and args.k is None and world == 1 and not args.no_side
     g = synth.make_graph(spec)
     k = spec["k"] if args.k is None else args.k
     s_host = synth.make_opinions(spec, g.n, k)  # n x k, column-major
@@ -529,6 +825,10 @@ def main():
         _, q, info = ctx.solve(gr, s_d, opts=opts, z_out=z_d)
         gr.free()
         return q, info
+
+    # the layout autotuner picks the row split for this graph (untimed); the
+    # timed steps then upload with the chosen layout
+    layout = tune_layout(ctx, fj, torch, g, s_d, stream) if not args.default_layout else None
 
     clocks = ClockSampler(local)
     with torch.cuda.stream(stream):
@@ -563,18 +863,11 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     value, total_ms = aggregate(float(sum(step_ms)), args.steps * k, dist, dev)
-
-    # roofline of the solve kernel (one cooperative launch per step for k <= 32)
-    kern_ms = float(np.mean([i["device_ms"] for i in infos]))
-    iters = int(np.mean([i["iterations"] for i in infos]))
-    refines = int(np.mean([i["refinements"] for i in infos]))
-    # iterations are the maximum over launches (k > 32), so for several
-    # launches the byte count is an upper bound
-    algo = sum(_bytes_per_launch(g.n, nnz, weighted, K, iters, refines) for K in _launch_widths(k))
-    achieved = algo / (kern_ms / 1000.0) / 1e9
-    widths = _launch_widths(k)
-    kernel_name = f"k_solve<float,{widths[0]}>" + (f" x {len(widths)} launches" if len(widths) > 1 else "")
     peak, peak_kind = _peaks()
+    rl = roofline(g, nnz, k, infos, peak)
+    rl["peak_kind"] = f"{peak_kind} (hbm_gbs, burst copy)"
+    rl["traffic"] = _profiled_traffic() if full else None
+    z_host = z_d.cpu().numpy() if full else None
 
     # solve-only rate on a resident graph (same opts), for context
     with torch.cuda.stream(stream):
@@ -600,24 +893,44 @@ def main():
     s_h = s_pin.T if k > 1 else s_pin.reshape(g.n)  # (n, k) column-major view
     z_h = torch.empty((k, g.n), dtype=torch.float64).pin_memory().numpy().T
     e2e_ms = []
-    for i in range(args.warmup + max(3, args.steps // 2)):
+    for i in range(3 + max(3, args.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         gr = ctx.upload(g.n, src_h, dst_h, w_h, merge_duplicates=MERGE)
         ctx.solve(gr, s_h, opts=opts, z_out=z_h)
         gr.free()
-        if i >= args.warmup:
+        if i >= 3:
             e2e_ms.append(1000 * (time.perf_counter() - t0))
     e2e_val, _ = aggregate(float(sum(e2e_ms)), len(e2e_ms) * k, dist, dev)
     h2d = g.m * 4 * (3 if weighted else 2) + g.n * k * 8
     d2h = g.n * k * 8 + k * 5 * 8
+    del src_h, dst_h, w_h, s_pin, z_h
 
-    compare = precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush) if full else None
-    warm = warm_start_run(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush) if full else None
-    lcc = lcc_run(ctx, torch, g, src_d, dst_d, w_d, stream) if full else None
-    small = small_graph_run(ctx, fj, torch, stream) if full else None
-    serving = serving_run(ctx, fj) if full and not args.no_serving else None
+    side = {"layout": layout}
+    ctx.set_layout()
+    if full:
+        side["precision_compare"] = precision_compare(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush, reps=3)
+        side["warm_start"] = warm_start_run(ctx, fj, torch, g, src_d, dst_d, w_d, stream, flush, reps=3)
+        del src_d, dst_d, w_d
+        torch.cuda.empty_cache()
+        subs = {}
+        for name, kk, st in SUB_WORKLOADS:
+            gg = g if name == args.workload else None
+            subs[f"{name}/k{kk}"] = sub_workload(ctx, fj, torch, name, kk, st, peak, flush, stream, gg)
+        side["workloads"] = subs
+        g2 = synth.make_graph(synth.WORKLOADS["cl_n1m_m5m_b2.3"])
+        side["lcc"] = lcc_run(ctx, torch, g2, torch.from_numpy(g2.src).to(dev),
+                              torch.from_numpy(g2.dst).to(dev), torch.from_numpy(g2.w).to(dev), stream)
+        side["small_graph"] = small_graph_run(ctx, fj, torch, stream)
+        side["batch"] = batch_run(ctx, fj, torch, stream)
+        if not args.no_serving:
+            side["serving"] = serving_run(ctx, fj, n_requests=args.serving_requests)
+            # the same stream's saturation with every request in its own launch
+            fj.serve_pack(ctx, 0)
+            side["serving"]["unpacked_saturation"] = serving_run(
+                ctx, fj, n_requests=args.serving_requests, rate_fracs=())["saturation"]
+            fj.serve_pack(ctx, 1 << 17)
 
     line = None
     if rank == 0:
@@ -625,25 +938,21 @@ def main():
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64", "data": "synthetic",
+            "dtype": "f32+df64 (float32 inner iterations, double-float refinement)", "data": "synthetic",
             "config": _workload_desc(spec, g, k, nnz),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                            "p99": float(np.percentile(step_ms, 99))},
-            "solve_only": {"value": 1000.0 / float(np.mean(solve_ms)), "unit": "solves/s",
+            "solve_only": {"value": k * 1000.0 / float(np.mean(solve_ms)), "unit": "solves/s",
                            "p50_ms": float(np.percentile(solve_ms, 50)),
                            "p99_ms": float(np.percentile(solve_ms, 99)),
                            "note": "resident graph, solve + quantities + z"},
-            "iterations": {"inner": iters, "refinements": refines,
+            "iterations": {"inner": rl["iterations"], "refinements": rl["refinements"],
                            "rel_residual": max(i["rel_residual"] for i in infos)},
             # nnz x k x inner iterations per second of the solve kernel, and
             # per second of the whole step
-            "edge_iterations_per_s": {"kernel": nnz * k * iters / (kern_ms / 1000.0),
-                                      "step": nnz * k * iters * value / k},
-            "roofline": {"kernel": kernel_name, "bound": "hbm", "achieved": achieved,
-                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": f"{peak_kind} (hbm_gbs, burst copy)",
-                         "traffic": _profiled_traffic() if full else None,
-                         "algorithmic_bytes": algo, "kernel_ms": kern_ms},
+            "edge_iterations_per_s": {"kernel": nnz * k * rl["iterations"] / (rl["kernel_ms"] / 1000.0),
+                                      "step": nnz * rl["iterations"] * value},
+            "roofline": rl,
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "p50_ms": float(np.percentile(e2e_ms, 50))},
             "gpu_launches": int(launches),
@@ -651,19 +960,22 @@ def main():
             "wall_s_timed": wall,
             "clocks": clk,
             "quantities": q[0],
-            "precision_compare": compare,
-            "warm_start": warm,
-            "lcc": lcc,
-            "small_graph": small,
-            "serving": serving,
+            **side,
         }
     ctx.close()
-    if rank == 0 and world == 1 and full and not args.no_cpu_baseline:
+    if rank == 0 and full and not args.no_cpu_baseline:
         s0 = s_host[:, 0]
-        v, dt = run_cpu_baseline(g, s0, args.cpu_solves)
+        acc = {args.workload: accuracy_bound(g, s0, z_host[0], q[0])}
+        v, desc, dt = cpu_sample(args.workload, g, s0)
         line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{args.cpu_solves} full oracle solves (FP64 CG to "
-                                          f"{TOL:g}) + quantities of the workload, {dt:.1f} s"}
+                                "sample": f"{desc} ({dt:.1f} s of CPU work)", **_host_info()}
+        # the 1M-node graph: the oracle's own full solve
+        spec2 = synth.WORKLOADS["cl_n1m_m5m_b2.3"]
+        s2 = synth.make_opinions(spec2, g2.n)[:, 0]
+        q2 = line["workloads"]["cl_n1m_m5m_b2.3/k1"].get("quantities")
+        if q2 is not None:
+            acc["cl_n1m_m5m_b2.3"] = {"sigma": accuracy_direct(g2, s2, q2)}
+        line["quantity_error"] = acc
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
