@@ -40,11 +40,12 @@ struct Layout {
   int32_t chunk_len = kChunkLen;
   int32_t sell_max = kSellMaxLen;
 };
-// Degree keys of the reordering sort saturate here (8-bit keys: one radix
-// pass).  Rows of more than kSellMaxLen entries come first either way, and
-// shorter rows are fully ordered by length; rows of degree >= kDegKeyMax
-// keep their input order among themselves.
-constexpr int kDegKeyMax = 255;
+// Degree keys of the reordering sort saturate here (16-bit keys: two radix
+// passes).  Rows are ordered by falling degree, except that rows of degree
+// >= kDegKeyMax come first and keep their input order among themselves; so
+// the rows of several chunks (degree > chunk length) form a prefix together
+// with those.
+constexpr int kDegKeyMax = 65535;
 
 // Error bits raised by device code.
 enum : int {

@@ -280,6 +280,7 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
   __shared__ int ex[K];             // e
   __shared__ int active[K], first[K], done[K], inner_ok[K];
   __shared__ int ctl_any_active, ctl_stop;
+  __shared__ int64_t n_multi_sh;
 
   const int warp = threadIdx.x >> 5;
   const int64_t n = P.sg.n;
@@ -347,6 +348,23 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
       mx = fmax(mx, x);
       nmn = fmax(nmn, -x);
       outside |= !(x >= 0.0 && x <= 1.0);
+    }
+    if (threadIdx.x == 0) {
+      // rows [0, n_multi) hold every row of several chunks: the rows of
+      // degree >= kDegKeyMax come first (in input order among themselves),
+      // then rows by falling degree, so "degree >= kDegKeyMax or several
+      // chunks" holds on a prefix.  The narrow kernels add these rows'
+      // chunk partials warp-wide in the passes after the walks.
+      int64_t lo = 0, hi = kWide ? 0 : P.sg.n_long;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (P.sg.row_ptr[mid + 1] - P.sg.row_ptr[mid] >= kDegKeyMax ||
+            P.sg.long_first[mid + 1] - P.sg.long_first[mid] >= 2)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      n_multi_sh = lo;
     }
     if (__syncthreads_or(outside) && threadIdx.x == 0) atomicOr(status, kWarnOpinionRange);
     const double v[1] = {acc};
@@ -425,8 +443,11 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
       double a_bb = 0, a_gam = 0, a_rr = 0, a_uu = 0;
       const double m = mu[c], scale = sc[c];
       const bool lz_col = P.paper && !(c & 1);
-      for (int64_t idx = gtid; idx < NK; idx += gstride) {
-        const int64_t i = idx / K;
+      // after a residual walk, rows of several chunks (narrow kernels) get
+      // their row sums warp-wide first, as in the vector update
+      const bool walked = !init || warm;
+      const int64_t n_multi = walked ? n_multi_sh : 0;
+      auto elem = [&](int64_t idx, int64_t i, bool given, VR lq_given) {
         VR sb, qv, lq;
         if (init) {
           const double sbd = (P.s[(int64_t)(c >> P.col_shift) * P.ld + P.perm[i]] - m) * scale;
@@ -435,7 +456,7 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
           a_bb += sbd * sbd;
           if (warm) {
             qv = P.q[idx];
-            lq = row_t<VR, K>(P.sg, P.t64, P.hub_part64, i, idx, c);
+            lq = given ? lq_given : row_t<VR, K>(P.sg, P.t64, P.hub_part64, i, idx, c);
           } else {
             P.q[idx] = zero;
             qv = zero;
@@ -444,7 +465,7 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
         } else {
           sb = P.sbar[idx];
           qv = P.q[idx];
-          lq = row_t<VR, K>(P.sg, P.t64, P.hub_part64, i, idx, c);
+          lq = given ? lq_given : row_t<VR, K>(P.sg, P.t64, P.hub_part64, i, idx, c);
         }
         const VR r64 = (sb - qv) - lq;
         a_rr64 += r64 * r64;
@@ -462,7 +483,36 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
         a_gam += (double)(rv * uv);
         a_rr += (double)(rv * rv);
         a_uu += (double)(uv * uv);
+      };
+      if constexpr (!kWide) {
+        const int lane = threadIdx.x & 31;
+        for (int64_t i = (int64_t)bid * kWarps + warp; i < n_multi; i += (int64_t)nb * kWarps) {
+          const int32_t f = P.sg.long_first[i], l = P.sg.long_first[i + 1];
+          VR ts[K];
+#pragma unroll
+          for (int cc = 0; cc < K; ++cc) ts[cc] = zero;
+          if (l - f == 1) {  // a row of one chunk: the walk wrote its sum
+#pragma unroll
+            for (int cc = 0; cc < K; ++cc)
+              if (lane == 0) ts[cc] = P.t64[i * K + cc];
+          }
+          for (int32_t q = f + lane; l - f > 1 && q < l; q += 32) {
+#pragma unroll
+            for (int cc = 0; cc < K; ++cc) ts[cc] += P.hub_part64[(int64_t)q * K + cc];
+          }
+#pragma unroll
+          for (int cc = 0; cc < K; ++cc) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) ts[cc] += shfl_xor_v(ts[cc], off);
+          }
+          VR lq = ts[0];
+#pragma unroll
+          for (int cc = 1; cc < K; ++cc)
+            if (lane == cc) lq = ts[cc];
+          if (lane < K) elem(i * K + lane, i, true, lq);
+        }
       }
+      for (int64_t idx = gtid + n_multi * K; idx < NK; idx += gstride) elem(idx, idx / K, false, zero);
       const double v[7] = {to_double(a_rr64), to_double(a_p), to_double(a_qs), to_double(a_ci),
                            a_gam, a_rr, a_uu};
       const int sl[7] = {S_RR64, S_P, S_QS, S_CI, S_GAM, S_RR, S_UU};
@@ -616,9 +666,61 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
         const float* __restrict__ vdinv = P.dinv;
         // the new u is the next walk's gathered vector: stored normally (it
         // stays in L2), the other vectors streamed in the narrow kernels
+        auto update = [&](int64_t idx, int64_t i, VI uv, VI tv, VI pv, VI dv, VI xv, VI rv, VI di, VI al_, VI be_) {
+          const VI wv = uv + tv;
+          const VI pn = uv + be_ * pv;
+          const VI dn = wv + be_ * dv;
+          const VI xn = xv + al_ * pn;
+          const VI rn = rv - al_ * dn;
+          const VI un = di * rn;
+          vst(vp + idx, pn);
+          vst(vd + idx, dn);
+          vst(vx + idx, xn);
+          vst(vr + idx, rn);
+          vu[idx] = un;
+          l_gam += rn * un;
+          l_rr += rn * rn;
+          l_uu += un * un;
+        };
+        // rows of several chunks (narrow kernels): one warp per row adds its
+        // chunk sums (lanes stride over the chunks, then the xor tree) and
+        // lane c updates the row's column c
+        const int64_t n_multi = n_multi_sh;
+        if constexpr (!kWide) {
+          const int lane = threadIdx.x & 31;
+          for (int64_t i = (int64_t)bid * kWarps + warp; i < n_multi; i += (int64_t)nb * kWarps) {
+            const int32_t f = P.sg.long_first[i], l = P.sg.long_first[i + 1];
+            VI ts[K];
+#pragma unroll
+            for (int cc = 0; cc < K; ++cc) ts[cc] = VI(0);
+            if (l - f == 1) {  // a row of one chunk: the walk wrote its sum
+#pragma unroll
+              for (int cc = 0; cc < K; ++cc)
+                if (lane == 0) ts[cc] = vt[i * K + cc];
+            }
+            for (int32_t q = f + lane; l - f > 1 && q < l; q += 32) {
+#pragma unroll
+              for (int cc = 0; cc < K; ++cc) ts[cc] += P.hub_part[(int64_t)q * K + cc];
+            }
+#pragma unroll
+            for (int cc = 0; cc < K; ++cc) {
+#pragma unroll
+              for (int off = 16; off > 0; off >>= 1) ts[cc] += shfl_xor_v(ts[cc], off);
+            }
+            VI tv = ts[0];
+#pragma unroll
+            for (int cc = 1; cc < K; ++cc)
+              if (lane == cc) tv = ts[cc];
+            if (lane < K) {
+              const int64_t idx = i * K + lane;
+              update(idx, i, vld(vu + idx), tv, fst ? VI(0) : vld(vp + idx), fst ? VI(0) : vld(vd + idx),
+                     vld(vx + idx), vld(vr + idx), vdinv[i], al, be);
+            }
+          }
+        }
         // kV elements per thread per round, all loads issued before use
         constexpr int kV = 2;
-        for (int64_t base = gtid; base < NK; base += kV * gstride) {
+        for (int64_t base = gtid + (kWide ? 0 : n_multi * K); base < NK; base += kV * gstride) {
           VI uv[kV], tv[kV], pv[kV], dv[kV], xv[kV], rv[kV], di[kV];
 #pragma unroll
           for (int e = 0; e < kV; ++e) {
@@ -637,22 +739,7 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
 #pragma unroll
           for (int e = 0; e < kV; ++e) {
             const int64_t idx = base + e * gstride;
-            if (idx < NK) {
-              const VI wv = uv[e] + tv[e];
-              const VI pn = uv[e] + be * pv[e];
-              const VI dn = wv + be * dv[e];
-              const VI xn = xv[e] + al * pn;
-              const VI rn = rv[e] - al * dn;
-              const VI un = di[e] * rn;
-              vst(vp + idx, pn);
-              vst(vd + idx, dn);
-              vst(vx + idx, xn);
-              vst(vr + idx, rn);
-              vu[idx] = un;
-              l_gam += rn * un;
-              l_rr += rn * rn;
-              l_uu += un * un;
-            }
+            if (idx < NK) update(idx, idx / K, uv[e], tv[e], pv[e], dv[e], xv[e], rv[e], di[e], al, be);
           }
         }
         a_gam = (double)l_gam;
