@@ -395,8 +395,9 @@ fj_status fj_tune_layout(fj_ctx* ctx, int64_t n, int64_t m, const int32_t* src,
  * admitted requests (default half the free memory when serving starts; <= 0
  * keeps the current value) and a cap on the thread blocks of each request's
  * solve (0, the default: the device's co-resident solve blocks divided by
- * max_inflight, so that the in-flight requests run side by side; < 0 keeps
- * the current value).
+ * max_inflight, so that the in-flight requests run side by side, and a
+ * quarter of them for a graph above the packing limit of fj_serve_pack, or
+ * above 131072 nodes when packing is off; < 0 keeps the current value).
  * Errors: FJ_ERR_ARG, FJ_ERR_CUDA. */
 fj_status fj_serve_config(fj_ctx* ctx, int32_t max_inflight,
                           int64_t mem_budget_bytes,

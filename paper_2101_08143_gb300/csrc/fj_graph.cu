@@ -40,11 +40,39 @@ constexpr int64_t kScanDirectTiles = 1024;
 
 // csrc/cdst/cw (nullable): the edge list is read from mapped host memory
 // and copied to these device arrays on the way.
+//
+// Degree counts: power-law graphs send millions of increments to each hub,
+// which serialize on one L2 address.  Each block therefore first counts in a
+// shared-memory table of kDegSlots nodes (claimed by the first node that
+// hashes to a slot; the hubs, being frequent, claim theirs early), and adds
+// the table to the global counts once at the end; other nodes go straight to
+// the global counts.  The counts are integers, so the result is exact.
+constexpr int kDegSlots = 2048;
+
+__device__ __forceinline__ void count_endpoint(int32_t v, int32_t* skey, int32_t* scnt, int32_t* deg) {
+  const unsigned slot = ((unsigned)v * 2654435761u) >> 21;  // 11 bits: kDegSlots slots
+  int32_t k = *reinterpret_cast<volatile int32_t*>(&skey[slot]);
+  if (k == -1) {
+    k = atomicCAS(&skey[slot], -1, v);
+    if (k == -1) k = v;
+  }
+  if (k == v)
+    atomicAdd(&scnt[slot], 1);
+  else
+    atomicAdd(&deg[v], 1);
+}
+
 __global__ void k_validate_degree(int64_t m, int64_t n, const int32_t* __restrict__ src,
                                   const int32_t* __restrict__ dst, const float* __restrict__ w,
                                   int64_t* __restrict__ err, int32_t* __restrict__ deg,
                                   int32_t* __restrict__ csrc, int32_t* __restrict__ cdst,
                                   float* __restrict__ cw) {
+  __shared__ int32_t skey[kDegSlots], scnt[kDegSlots];
+  for (int i = threadIdx.x; i < kDegSlots; i += blockDim.x) {
+    skey[i] = -1;
+    scnt[i] = 0;
+  }
+  __syncthreads();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t u = src[e], v = dst[e];
@@ -63,10 +91,13 @@ __global__ void k_validate_degree(int64_t m, int64_t n, const int32_t* __restric
       atomicOr(reinterpret_cast<unsigned long long*>(&err[0]), (unsigned long long)bad);
       atomicMin(reinterpret_cast<unsigned long long*>(&err[1]), (unsigned long long)e);
     } else if (u != v) {
-      atomicAdd(&deg[u], 1);
-      atomicAdd(&deg[v], 1);
+      count_endpoint(u, skey, scnt, deg);
+      count_endpoint(v, skey, scnt, deg);
     }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kDegSlots; i += blockDim.x)
+    if (skey[i] >= 0 && scnt[i] > 0) atomicAdd(&deg[skey[i]], scnt[i]);
 }
 
 // ------------------------------------------------------------- radix sort

@@ -171,10 +171,18 @@ size_t estimate_bytes(const Request& r, int num_sms) {
 
 // Grid cap of one request's solve: the configured one, else the device's
 // co-resident solve blocks (two per SM) shared by the in-flight requests, so
-// that they run side by side instead of one at a time.
-int block_cap(const Server& S) {
+// that they run side by side instead of one at a time; a request larger than
+// the packing limit (a graph of more than pack_max_nodes nodes, or of more
+// than 131072 when packing is off) may use a quarter of them, since its
+// latency grows with its work.  The cap depends only on the request and the
+// configuration, never on the load, so a request's results are the same bits
+// alone or in a mix.
+int block_cap(const Server& S, const Request& r) {
   if (S.max_blocks > 0) return S.max_blocks;
-  return std::max(1, 2 * S.num_sms / std::max(1, S.max_inflight));
+  const int share = std::max(1, 2 * S.num_sms / std::max(1, S.max_inflight));
+  const int64_t limit = S.pack_max_nodes > 0 ? S.pack_max_nodes : (int64_t)1 << 17;
+  if (request_n(r) > limit) return std::max(share, 2 * S.num_sms / 4);
+  return share;
 }
 
 // Launch widths of k columns: 32 at a time, then 16, 8, 4, 2, 1.
@@ -623,7 +631,7 @@ void worker_loop(Server* Sp) {
       while (S.slots[slot].busy) ++slot;
       S.slots[slot].busy = true;
       r->slot = slot;
-      r->block_cap = block_cap(S);
+      r->block_cap = block_cap(S, *r);
       S.used += (int64_t)r->mem_est;
       ++S.admitted;
       r->t_start = std::chrono::steady_clock::now();

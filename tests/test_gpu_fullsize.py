@@ -1,10 +1,13 @@
-"""Parity at the full sizes of the large workloads, where the oracle cannot
-solve the whole system in reasonable time.  Checked instead, with the oracle's
-own code on the GPU's z:
-  * the residual (s - (I + L) z)_i on sampled rows and on the hub rows,
-    evaluated edge by edge in float64 (oracle.residual_rows);
-  * the five quantities by their definitions (Sec. 3.2) applied to z, against
-    the values the kernel reduced on the device;
+"""Parity at the full sizes of the large workloads, where the oracle's own
+solve takes minutes.  Checked instead, with the oracle's code on the GPU's z:
+  * the full float64 residual r = s - (I + L) z, over every edge
+    (oracle.apply_i_plus_l): ||r|| <= tol ||s_bar||;
+  * since I + L has no eigenvalue below 1, ||z - z*|| <= ||r||, and each
+    quantity is ||a||^2 for a vector a that moves with z by at most ||r||
+    (Sec. 3.2 definitions, Lemma PropA), so |q(z) - q(z*)| <= ||r|| (2
+    sqrt(q(z)) + ||r||); with the distance between the device's reduction
+    and the definitions on z, this bounds each quantity's error against the
+    exact solution, which must be below 1e-6 relative;
   * the identities D + C = s^T z (Sec. 3.2), C_I + 2D + C = ||s||^2 and
     conservation sum z = sum s (Sec. 3.1).
 """
@@ -28,19 +31,18 @@ def ctx():
     c.close()
 
 
-def _check_column(g, s, z, q, tol_rel, rng):
+def _check_column(g, s, z, q, tol_rel, tol_res):
     n = g.n
-    # residual on sampled rows + the 64 highest-degree rows
-    deg = np.bincount(g.src, minlength=n) + np.bincount(g.dst, minlength=n)
-    rows = np.unique(np.concatenate([rng.integers(0, n, 2000), np.argsort(-deg)[:64]]))
     sbar = s - s.mean()
-    res = fo.residual_rows(n, g.src, g.dst, g.w, z, s, rows)
-    scale = np.sqrt(np.sum(sbar ** 2) / n)  # rms of s_bar
-    assert np.max(np.abs(res)) <= 1e-6 * scale * np.sqrt(n), np.max(np.abs(res))
-    # the device-reduced quantities equal the definitions on z
+    r = s - fo.apply_i_plus_l(n, g.src, g.dst, g.w, z)
+    eps = float(np.sqrt(r @ r))
+    assert eps <= tol_res * float(np.sqrt(sbar @ sbar)), eps
     qd = fo.quantities_from_z(n, g.src, g.dst, g.w, s, z)
+    dev = {name: eps * (2.0 * np.sqrt(qd[name]) + eps) for name in ("C_I", "D", "P", "C")}
+    dev["I_dc"] = dev["D"] + dev["C"]
     for name in fo.QUANTITY_NAMES:
-        assert fo.relative_error(qd[name], q[name], 1e-12 * float(s @ s)) <= tol_rel, (name, q[name], qd[name])
+        bound = (abs(q[name] - qd[name]) + dev[name]) / (qd[name] - dev[name])
+        assert bound <= tol_rel, (name, q[name], qd[name], bound)
     # identities
     assert q["I_dc"] == pytest.approx(float(s @ z), rel=tol_rel)
     assert q["C_I"] + 2 * q["D"] + q["C"] == pytest.approx(float(s @ s), rel=tol_rel)
@@ -61,13 +63,13 @@ def test_chung_lu_20m_150m(ctx):
         sd = torch.from_numpy(s).to(dev)
         z, q, info = ctx.solve(dg, sd, opts=fj.default_opts(tol=1e-8))
     assert info["rel_residual"] <= 1e-8
-    _check_column(g, s, z.cpu().numpy(), q[0], 1e-6, np.random.default_rng(5))
+    _check_column(g, s, z.cpu().numpy(), q[0], 1e-6, 1.01e-8)
 
 
 def test_chung_lu_4m_40m_k256(ctx):
     """n = 4,000,000, m = 40,000,000, exponent 2.1, unit weights, k = 256
     (half uniform, half Beta(1/2, 1/2) opinions), launched as 8 x 32
-    columns; 16 columns are checked."""
+    columns; 16 columns (two of every launch) are checked in full."""
     import torch
     from paper_2101_08143_gb300 import fj
     spec = synth.WORKLOADS["cl_n4m_m40m_b2.1_k256"]
@@ -79,6 +81,5 @@ def test_chung_lu_4m_40m_k256(ctx):
         z, q, info = ctx.solve(dg, sd, opts=fj.default_opts(tol=1e-8))
     assert info["rel_residual"] <= 1e-8
     zh = z.cpu().numpy()
-    rng = np.random.default_rng(3)
     for j in list(range(0, 256, 32)) + list(range(17, 256, 32)):
-        _check_column(g, s[:, j], zh[j], q[j], 1e-6, rng)
+        _check_column(g, s[:, j], zh[j], q[j], 1e-6, 1.01e-8)

@@ -105,6 +105,28 @@ def test_bench_workload_full_size(ctx):
     _check_quantities(q[0], qo[0], s, 1e-6)
 
 
+def test_bench_workload_pure_float32(ctx):
+    """The 1M-node bench graph in the pure float32 mode (one float32 PCG solve
+    to relative residual 1e-6, no refinement): every quantity within 1e-3 of
+    the oracle (the float32 tolerance)."""
+    import torch
+    from paper_2101_08143_gb300 import fj
+    spec = synth.WORKLOADS["cl_n1m_m5m_b2.3"]
+    g = synth.make_graph(spec)
+    s = synth.make_opinions(spec, g.n)[:, 0]
+    zo, qo = _oracle(g, s)
+    dev = torch.device("cuda")
+    with ctx.upload(g.n, torch.from_numpy(g.src).to(dev), torch.from_numpy(g.dst).to(dev),
+                    torch.from_numpy(g.w).to(dev), merge_duplicates=True) as dg:
+        z, q, info = ctx.solve(dg, torch.from_numpy(s).to(dev),
+                               opts=fj.default_opts(tol=1e-6, precision=fj.PREC_FP32))
+    assert info["refinements"] <= 1
+    _check_quantities(q[0], qo[0], s, 1e-3)
+    # ||z - z*|| <= ||s_bar - (I + L) q|| (no eigenvalue of I + L below 1)
+    bound = 1.01 * info["rel_residual"] * float(np.linalg.norm(s - s.mean()))
+    assert float(np.max(np.abs(z.cpu().numpy() - zo[:, 0]))) <= bound
+
+
 @pytest.mark.parametrize("n,m,weighted,seed", [(300, 900, True, 1), (1000, 20000, True, 2),
                                                (4097, 9000, False, 3), (12345, 60000, True, 4)])
 def test_random_graphs_several_tiles(ctx, n, m, weighted, seed):
