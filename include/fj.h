@@ -79,6 +79,20 @@ enum {
  * I_dc = D + C.  z is z~.  The default (one centred solve, z = q + mu 1)
  * gives the same values in exact arithmetic at half the work. */
 #define FJ_TWO_SOLVES 4u
+/* Solve option (fj_opts.flags; every solve call and fj_submit, not with
+ * FJ_TWO_SOLVES or FJ_PREC_FP32): opts.tol bounds the relative error of each
+ * of the five quantities against the exact solution, instead of the
+ * relative residual.  The bound is certified at each float64 residual
+ * evaluation from eps = ||s_bar - (I+L) q|| alone: (I+L) has no eigenvalue
+ * below 1, so the error e of the iterate has ||e|| <= eps and
+ * e^T L e <= eps^2; each of C_I, D, P, C is a squared norm of a vector that
+ * moves with the iterate by e, its centred part or W^1/2 B e, so it is off by
+ * at most eps (2 sqrt(x) + eps) where x is its value at the iterate, and
+ * I_dc = D + C by the sum of two such terms.  The solve stops once every
+ * such bound, relative to x minus the bound, is at most tol / 2 (half kept
+ * as margin for rounding); a quantity equal to zero bounds nothing.
+ * info->rel_residual still reports the relative residual reached. */
+#define FJ_QUANTITY_TOL 8u
 
 /* Arithmetic of the solve (fj_opts.precision). */
 enum {

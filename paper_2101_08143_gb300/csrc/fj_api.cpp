@@ -543,8 +543,12 @@ static fj_status solve_impl(fj_ctx* c, const fj_graph* g, int32_t k, const doubl
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || o.max_iter < 1 ||
       o.max_refine < 1 || o.precision < 0 || o.precision > 2 ||
-      (o.flags & ~(FJ_DEVICE_PTRS | FJ_MERGE_DUPLICATES | FJ_TWO_SOLVES))) {
+      (o.flags & ~(FJ_DEVICE_PTRS | FJ_MERGE_DUPLICATES | FJ_TWO_SOLVES | FJ_QUANTITY_TOL))) {
     set_error("fj_solve: invalid options");
+    return FJ_ERR_ARG;
+  }
+  if ((o.flags & FJ_QUANTITY_TOL) && ((o.flags & FJ_TWO_SOLVES) || o.precision == FJ_PREC_FP32)) {
+    set_error("fj_solve: FJ_QUANTITY_TOL needs the one-solve form and a refined precision (MIXED or FP64)");
     return FJ_ERR_ARG;
   }
   FJ_CUDA(cudaSetDevice(c->device));
@@ -809,8 +813,9 @@ static fj_status check_serve_args(int32_t k, const double* s, const fj_opts* opt
   fj_default_opts(o);
   if (opts) *o = *opts;
   if (!(o->tol > 0.0) || !(o->inner_tol > 0.0) || o->inner_tol >= 1.0 || o->max_iter < 1 || o->max_refine < 1 ||
-      o->precision < 0 || o->precision > 2 || (o->flags & FJ_TWO_SOLVES)) {
-    set_error("fj_submit: invalid options (FJ_TWO_SOLVES is for fj_solve_ex)");
+      o->precision < 0 || o->precision > 2 || (o->flags & FJ_TWO_SOLVES) ||
+      ((o->flags & FJ_QUANTITY_TOL) && o->precision == FJ_PREC_FP32)) {
+    set_error("fj_submit: invalid options (FJ_TWO_SOLVES is for fj_solve_ex; FJ_QUANTITY_TOL needs MIXED or FP64)");
     return FJ_ERR_ARG;
   }
   return FJ_OK;

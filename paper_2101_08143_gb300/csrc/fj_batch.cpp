@@ -68,8 +68,9 @@ extern "C" fj_status fj_solve_batch(fj_ctx* c, int32_t count, const fj_graph* co
   fj_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || o.max_iter < 1 || o.max_refine < 1 ||
-      o.precision < 0 || o.precision > 2 || (o.flags & ~(FJ_DEVICE_PTRS | FJ_MERGE_DUPLICATES))) {
-    set_error("fj_solve_batch: invalid options (FJ_TWO_SOLVES is for fj_solve_ex)");
+      o.precision < 0 || o.precision > 2 || (o.flags & ~(FJ_DEVICE_PTRS | FJ_MERGE_DUPLICATES | FJ_QUANTITY_TOL)) ||
+      ((o.flags & FJ_QUANTITY_TOL) && o.precision == FJ_PREC_FP32)) {
+    set_error("fj_solve_batch: invalid options (FJ_TWO_SOLVES is for fj_solve_ex; FJ_QUANTITY_TOL needs MIXED or FP64)");
     return FJ_ERR_ARG;
   }
   int device = 0, num_sms = 0;

@@ -11,7 +11,8 @@
 //      the SpMV layouts: chunks of the long rows, sliced ELL for the rest,
 //      and the work units;
 //   3. one streaming pass writes the 2m directed entries in solver
-//      numbering; a stable LSD radix sort of them by row puts every entry at
+//      numbering; a stable LSD radix sort of them by row (digits of 8 or 9
+//      bits, whichever takes fewer passes) puts every entry at
 //      its CSR position, rows keeping the input order of their entries, and
 //      its last pass also writes the sliced-ELL copy;
 //   4. the Jacobi preconditioner 1 / (1 + d_i).
@@ -151,10 +152,16 @@ struct EntryDst {
   float* sell_val;
 };
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t N, int shift,
+// Digits of up to kBits bits: 8 in general; 9 where that saves a pass
+// (keys of 25 to 27 bits sort in 3 passes instead of 4).  The digit of a pass
+// is (key >> shift) & (2^width - 1) with width <= kBits.
+template <int kBits>
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t N, int shift, int width,
                                                              int32_t* __restrict__ hist) {
-  __shared__ int h[256];
-  for (int i = threadIdx.x; i < 256; i += kSortThreads) h[i] = 0;
+  constexpr int kD = 1 << kBits;
+  __shared__ int h[kD];
+  const int D = 1 << width, mask = D - 1;
+  for (int i = threadIdx.x; i < D; i += kSortThreads) h[i] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortChunk;
   for (int i = threadIdx.x; i < kSortChunk; i += kSortThreads) {
@@ -163,11 +170,11 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t
       int32_t key, col;
       float val;
       load_entry(s, p, key, col, val);
-      atomicAdd(&h[(key >> shift) & 255], 1);
+      atomicAdd(&h[(key >> shift) & mask], 1);
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 256; i += kSortThreads) hist[(int64_t)i * gridDim.x + blockIdx.x] = h[i];
+  for (int i = threadIdx.x; i < D; i += kSortThreads) hist[(int64_t)i * gridDim.x + blockIdx.x] = h[i];
 }
 
 // Stable scatter of one chunk of kSortChunk items.  Items are ranked in
@@ -176,24 +183,29 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t
 // global stores are coalesced.  LAST: the sorted position is
 // the entry's CSR position; write the CSR and sliced-ELL copies instead of
 // the sort buffers (entries keyed n are dropped).
+template <int kBits>
 struct ScatterSmem {
   int32_t key[kSortChunk];
   int32_t col[kSortChunk];
   float val[kSortChunk];
-  int wcnt[kSortThreads / 32][256];
-  int run[256];
-  int start[256];
+  int wcnt[kSortThreads / 32][1 << kBits];
+  int run[1 << kBits];
+  int start[1 << kBits];
 };
 
-template <bool LAST>
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int64_t N, int shift,
+template <bool LAST, int kBits>
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int64_t N, int shift, int width,
                                                                 const int32_t* __restrict__ offs,
                                                                 int32_t* __restrict__ okey,
                                                                 int32_t* __restrict__ ocol,
                                                                 float* __restrict__ oval, EntryDst d) {
   constexpr int kW = kSortThreads / 32;
+  constexpr int kD = 1 << kBits;
+  constexpr int kPer = kD / 32;  // digits per lane in the scan of the counts
+  static_assert(kD <= kSortThreads, "one thread per digit");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
+  ScatterSmem<kBits>& sm = *reinterpret_cast<ScatterSmem<kBits>*>(smem_raw);
+  const int D = 1 << width, mask = D - 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int64_t cbase = (int64_t)blockIdx.x * kSortChunk;
@@ -202,7 +214,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
   // input order is (warp, round, lane): each warp ranks its own items
   // against warp-private digit counters, and one block-wide pass turns the
   // counters into per-warp offsets
-  for (int j = lane; j < 256; j += 32) sm.wcnt[warp][j] = 0;
+  for (int j = lane; j < kD; j += 32) sm.wcnt[warp][j] = 0;
   int32_t key[kSortItems], col[kSortItems];
   float val[kSortItems];
   int rank[kSortItems];
@@ -219,7 +231,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const bool valid = wbase + r * 32 + lane < cnt;
-    const int digit = valid ? ((key[r] >> shift) & 255) : 256;
+    const int digit = valid ? ((key[r] >> shift) & mask) : kD;
     const unsigned peers = __match_any_sync(kFull, digit);
     const int rk = __popc(peers & lt_mask);
     const int before = valid ? sm.wcnt[warp][digit] : 0;
@@ -229,7 +241,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
     rank[r] = before + rk;
   }
   __syncthreads();
-  if (tid < 256) {  // per digit: offsets of the warps' runs, and the total
+  if (tid < kD) {  // per digit: offsets of the warps' runs, and the total
     int acc = 0;
 #pragma unroll
     for (int w = 0; w < kW; ++w) {
@@ -240,12 +252,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
     sm.run[tid] = acc;
   }
   __syncthreads();
-  // chunk-local start of every digit: exclusive scan of the 256 counts
+  // chunk-local start of every digit: exclusive scan of the kD counts
   if (warp == 0) {
-    int v[8], sum = 0;
+    int v[kPer], sum = 0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      v[q] = sm.run[lane * 8 + q];
+    for (int q = 0; q < kPer; ++q) {
+      v[q] = sm.run[lane * kPer + q];
       sum += v[q];
     }
     int incl = sum;
@@ -256,8 +268,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
     }
     int excl = incl - sum;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      sm.start[lane * 8 + q] = excl;
+    for (int q = 0; q < kPer; ++q) {
+      sm.start[lane * kPer + q] = excl;
       excl += v[q];
     }
   }
@@ -265,7 +277,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     if (wbase + r * 32 + lane < cnt) {
-      const int digit = (key[r] >> shift) & 255;
+      const int digit = (key[r] >> shift) & mask;
       const int pos = sm.start[digit] + sm.wcnt[warp][digit] + rank[r];
       sm.key[pos] = key[r];
       sm.col[pos] = col[r];
@@ -276,7 +288,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
   const int64_t n_long = LAST ? d.cnt[0] : 0;
   for (int i = tid; i < cnt; i += kSortThreads) {
     const int32_t k = sm.key[i];
-    const int digit = (k >> shift) & 255;
+    const int digit = (k >> shift) & mask;
     const int64_t pos = (int64_t)offs[(int64_t)digit * gridDim.x + blockIdx.x] + (i - sm.start[digit]);
     if (LAST) {
       if (k < s.n) {
@@ -736,50 +748,62 @@ static unsigned grid_for(int64_t work, int threads) {
   return (unsigned)b;
 }
 
-// Stable LSD radix sort (8-bit digits) of N entries by key in [0, key_max],
-// from buffer set 0.  Buffers kb/cb/vb[2] must hold N + kPad elements (vb
-// may be null: no val); returns the index (0/1) of the buffer set holding
-// the result.  With `last`, the last pass writes the CSR and sliced ELL
-// instead.
-static fj_status radix_sort(int32_t n, int64_t N, int64_t key_max, int32_t* kb[2], int32_t* cb[2], float* vb[2],
-                            const EntryDst* last, cudaStream_t st, int* result) {
-  int bits = 1;
-  while ((int64_t(1) << bits) <= key_max) ++bits;
-  const int passes = (bits + 7) / 8;
+// Stable LSD radix sort of N entries by key in [0, key_max], from buffer set
+// 0, in the fewest passes of digits of at most 8 bits, or of 9 bits where
+// that takes one pass fewer.  Buffers kb/cb/vb[2] must hold N + kPad
+// elements (vb may be null: no val); returns the index (0/1) of the buffer
+// set holding the result.  With `last`, the last pass writes the CSR and
+// sliced ELL instead.  The result is the unique stable order, whatever the
+// digit widths.
+template <int kBits>
+static fj_status radix_passes(int32_t n, int64_t N, int bits, int32_t* kb[2], int32_t* cb[2], float* vb[2],
+                              const EntryDst* last, cudaStream_t st, int* result) {
+  const int passes = (bits + kBits - 1) / kBits;
   const int64_t nblocks = (N + kSortChunk - 1) / kSortChunk;
   int cur = 0;
   *result = 0;
   if (N == 0) return FJ_OK;
   int32_t* h = nullptr;
-  FJ_CUDA(malloc_async(&h, 256 * nblocks * sizeof(int32_t), st));
+  FJ_CUDA(malloc_async(&h, ((int64_t)1 << kBits) * nblocks * sizeof(int32_t), st));
   fj_status rc = FJ_OK;
-  const size_t ssm = sizeof(ScatterSmem);
+  const size_t ssm = sizeof(ScatterSmem<kBits>);
   const EntryDst none{};
+  int shift = 0;
   for (int pass = 0; pass < passes && rc == FJ_OK; ++pass) {
+    // widths differ by at most one bit, the wider ones first
+    const int width = bits / passes + (pass < bits % passes ? 1 : 0);
     const bool fin = last && pass == passes - 1;
     const EntrySrc s{kb[cur], cb[cur], vb[cur], n};
     const int dstb = 1 - cur;
-    const int shift = pass * 8;
     count_launches(2);
-    k_radix_hist<<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, shift, h);
-    rc = exclusive_scan<int32_t>(h, 256 * nblocks, st);
+    k_radix_hist<kBits><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, shift, width, h);
+    rc = exclusive_scan<int32_t>(h, ((int64_t)1 << width) * nblocks, st);
     if (rc != FJ_OK) break;
     const EntryDst& d = fin ? *last : none;
     auto launch = [&](auto kern) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
-      kern<<<(unsigned)nblocks, kSortThreads, ssm, st>>>(s, N, shift, h, kb[dstb], cb[dstb], vb[dstb], d);
+      kern<<<(unsigned)nblocks, kSortThreads, ssm, st>>>(s, N, shift, width, h, kb[dstb], cb[dstb], vb[dstb], d);
     };
     if (fin)
-      launch(k_radix_scatter<true>);
+      launch(k_radix_scatter<true, kBits>);
     else
-      launch(k_radix_scatter<false>);
+      launch(k_radix_scatter<false, kBits>);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "radix sort");
     cur = dstb;
+    shift += width;
   }
   cudaFreeAsync(h, st);
   *result = cur;
   return rc;
+}
+
+static fj_status radix_sort(int32_t n, int64_t N, int64_t key_max, int32_t* kb[2], int32_t* cb[2], float* vb[2],
+                            const EntryDst* last, cudaStream_t st, int* result) {
+  int bits = 1;
+  while ((int64_t(1) << bits) <= key_max) ++bits;
+  if ((bits + 8) / 9 < (bits + 7) / 8) return radix_passes<9>(n, N, bits, kb, cb, vb, last, st, result);
+  return radix_passes<8>(n, N, bits, kb, cb, vb, last, st, result);
 }
 
 }  // namespace fj

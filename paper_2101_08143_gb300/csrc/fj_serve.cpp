@@ -290,7 +290,7 @@ fj_status start_solve(Server& S, Request* r) {
   cudaMemcpyAsync(ds, r->s.data(), (size_t)n * r->k * 8, cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(dstat, 0, (size_t)launches * 12, st);
   fj_opts o = r->opts;
-  o.flags = FJ_DEVICE_PTRS;
+  o.flags = FJ_DEVICE_PTRS | (r->opts.flags & FJ_QUANTITY_TOL);
   fj_status rc = fj_solve_device(g, st, S.num_sms, r->k, ds, nullptr, dq, dres, dstat, r->dev + s_bytes + small,
                                  ws, o, &r->launches, r->block_cap, nullptr, &r->info.blocks);
   if (rc != FJ_OK) return rc;
@@ -417,7 +417,7 @@ fj_status start_batch(Server& S, Batch& B) {
         it.ws_bytes = pt.ws;
         it.blocks = pt.blocks;
         it.opts = r->opts;
-        it.opts.flags = FJ_DEVICE_PTRS;
+        it.opts.flags = FJ_DEVICE_PTRS | (r->opts.flags & FJ_QUANTITY_TOL);
         woff += (pt.ws + 255) & ~size_t(255);
         r->info.blocks = std::max(r->info.blocks, pt.blocks);
         items.push_back(it);

@@ -98,6 +98,7 @@ struct SolveParams {
   int max_iter;
   int max_refine;
   int mode;
+  int qtol;  // tol bounds each quantity's relative error (FJ_QUANTITY_TOL)
   // two-solve mode (Algorithm 1 as printed): launch columns come in pairs
   // (2j: s_j solved as is, 2j+1: s_j centred), source column = c >> col_shift
   int paper;
@@ -205,6 +206,36 @@ __device__ __forceinline__ void grid_reduce(const int (&slots)[NS], const double
 }
 
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+// Largest residual norm eps = ||s_bar - (I+L) q|| at which every quantity
+// evaluated at the iterate is certified within relative error t of its
+// value at the exact solution.  (I + L) has no eigenvalue below 1, so the
+// error e = (I+L)^-1 r has ||e|| <= eps and e^T L e <= r^T (I+L)^-1 r <=
+// eps^2.  Each of C_I, D, P, C is ||a||^2 for a vector a that moves with the
+// iterate by e, the centred e, or W^1/2 B e (Sec. 3.2 definitions), so it is
+// off by at most eps (2 ||a|| + eps); I_dc = D + C by the sum of two such
+// terms.  A relative error of at most t needs dev <= t (x - dev), i.e.
+// dev <= t' x with t' = t / (1 + t): the positive root of
+// eps^2 + 2 a eps = t' x, written stably.  Zero quantities bound nothing.
+__device__ __forceinline__ double quantity_eps(double CI, double D, double Pq, double C, double t) {
+  const double tp = t / (1.0 + t);
+  double best = INFINITY;
+  const double xs[4] = {CI, D, Pq, C};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const double x = xs[j];
+    if (x > 0.0) {
+      const double a = sqrt(x);
+      best = fmin(best, tp * x / (a + sqrt(a * a + tp * x)));
+    }
+  }
+  const double I = D + C;  // 2 eps^2 + 2 (a_D + a_C) eps = t' I
+  if (I > 0.0) {
+    const double b = sqrt(fmax(D, 0.0)) + sqrt(fmax(C, 0.0));
+    best = fmin(best, tp * I / (b + sqrt(b * b + 2.0 * tp * I)));
+  }
+  return best;
+}
 
 // SpMM walk for K >= 8: the warps of the whole grid take work units one at a
 // time from one counter, in unit order (hub chunks first, then slices by
@@ -560,12 +591,31 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
         P.resid[cc] = rel;
       }
       bool conv = (bb[cc] == 0.0) || (rel <= P.tol);
+      // residual-norm reduction the next inner solve should reach
+      double need = (rr64 > 0.0) ? 0.5 * P.tol * sqrt(bb[cc] / rr64) : 1.0;
+      if (P.qtol) {
+        // certified per-quantity rule, with half of tol kept as margin; the
+        // first pass (q = 0 or z0) only sets the first inner solve's goal
+        if (init) {
+          need = 0.1 * P.tol;
+          conv = bb[cc] == 0.0;
+        } else {
+          const int e2 = 2 * ex[cc];
+          const double m = mu[cc];
+          const double Pq = ldexp(res[S_P * K + cc], e2);
+          const double eps_goal =
+              quantity_eps(ldexp(res[S_CI * K + cc], e2), ldexp(0.5 * res[S_D * K + cc], e2), Pq,
+                           Pq + 2.0 * m * ldexp(res[S_QS * K + cc], ex[cc]) + (double)n * m * m, 0.5 * P.tol);
+          const double eps = ldexp(sqrt(rr64), ex[cc]);
+          conv = bb[cc] == 0.0 || eps <= eps_goal;
+          need = (eps > 0.0) ? 0.5 * fmin(eps_goal / eps, 1.0) : 1.0;
+        }
+      }
       if (fp32_mode && !init) conv = inner_ok[cc] || bb[cc] == 0.0;  // one inner solve only
       if (!done[cc] && conv) done[cc] = 1;
       // next inner solve for columns not done
       const double rr = res[S_RR * K + cc];
       double goal = P.inner_tol;
-      const double need = (rr64 > 0.0) ? 0.5 * P.tol * sqrt(bb[cc] / rr64) : 1.0;
       if (P.mode == kModeFP64) goal = need;
       else if (need > goal) goal = need;
       if (fp32_mode) goal = P.tol;
@@ -937,6 +987,7 @@ static fj_status fill_params(SolveParams<VI>& P, const fj_graph* g, const double
   P.max_iter = o.max_iter;
   P.max_refine = o.max_refine;
   P.mode = mode;
+  P.qtol = (o.flags & FJ_QUANTITY_TOL) ? 1 : 0;
   P.paper = paper ? 1 : 0;
   P.z0 = z0;
   P.col_shift = paper ? 1 : 0;
@@ -1195,8 +1246,9 @@ extern "C" fj_status fj_solve_fixed(const fj_graph* g, void* stream, int32_t k, 
   fj_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || o.max_iter < 1 ||
-      o.max_refine < 1 || o.precision < 0 || o.precision > 2 || (o.flags & FJ_TWO_SOLVES)) {
-    set_error("fj_solve_fixed: invalid options (FJ_TWO_SOLVES is for fj_solve_ex)");
+      o.max_refine < 1 || o.precision < 0 || o.precision > 2 || (o.flags & FJ_TWO_SOLVES) ||
+      ((o.flags & FJ_QUANTITY_TOL) && o.precision == FJ_PREC_FP32)) {
+    set_error("fj_solve_fixed: invalid options (FJ_TWO_SOLVES is for fj_solve_ex; FJ_QUANTITY_TOL needs MIXED or FP64)");
     return FJ_ERR_ARG;
   }
   FJ_CUDA(cudaSetDevice(g->device));
@@ -1246,7 +1298,7 @@ extern "C" fj_status fj_solve_fixed(const fj_graph* g, void* stream, int32_t k, 
   cudaStream_t st = (cudaStream_t)stream;
   FJ_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int) * 3 * 6, st));
   fj_opts od = o;
-  od.flags = FJ_DEVICE_PTRS;
+  od.flags = FJ_DEVICE_PTRS | (o.flags & FJ_QUANTITY_TOL);
   int done = 0, grid = 0;
   rc = fj_solve_device(g, st, num_sms, k, s, z, dq, dres, dstat, base + head, FJ_FIXED_SCRATCH_BYTES - head, od,
                        &done, 0, nullptr, &grid);

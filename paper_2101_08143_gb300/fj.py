@@ -30,6 +30,7 @@ FJ_HOST_PTRS = 0
 FJ_DEVICE_PTRS = 1
 FJ_MERGE_DUPLICATES = 2
 FJ_TWO_SOLVES = 4
+FJ_QUANTITY_TOL = 8
 FJ_WARN_OPINION_RANGE = 1
 
 PREC_MIXED = 0

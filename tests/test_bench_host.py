@@ -2,9 +2,11 @@
 byte model behind roofline.achieved, the link between the committed ncu
 profile and the kernel sources, and the clock sampler's choice of samples."""
 import datetime
+import math
 import os
 import time
 
+import numpy as np
 import pytest
 
 import bench
@@ -102,3 +104,34 @@ def test_quantity_error_bound_holds(seed):
             true_err = abs(q_gpu[name] - q_star[name]) / q_star[name]
             assert true_err <= bound[name], (name, scale, true_err, bound[name])
             assert bound[name] < 1.0
+
+
+def _stopping_rule_eps(q, t):
+    """The largest residual norm the solver's FJ_QUANTITY_TOL rule accepts
+    for target t (the device computes the same roots)."""
+    tp = t / (1.0 + t)
+    best = math.inf
+    for name in ("C_I", "D", "P", "C"):
+        x = q[name]
+        if x > 0:
+            a = math.sqrt(x)
+            best = min(best, tp * x / (a + math.sqrt(a * a + tp * x)))
+    i_dc = q["D"] + q["C"]
+    if i_dc > 0:
+        b = math.sqrt(q["D"]) + math.sqrt(q["C"])
+        best = min(best, tp * i_dc / (b + math.sqrt(b * b + 2.0 * tp * i_dc)))
+    return best
+
+
+def test_stopping_rule_target_inverts_the_certified_bound():
+    """At the residual norm the stopping rule accepts, the certified bound
+    of the binding quantity equals the target; any larger norm exceeds it."""
+    rng = np.random.default_rng(71)
+    for _ in range(300):
+        q = {name: float(10.0 ** rng.uniform(-3, 8)) for name in ("C_I", "D", "P", "C")}
+        q["I_dc"] = q["D"] + q["C"]
+        t = float(10.0 ** rng.uniform(-10, -2))
+        eps = _stopping_rule_eps(q, t)
+        worst = max(bench.quantity_error_bound(q, q, eps).values())
+        assert t * (1 - 1e-6) <= worst <= t * (1 + 1e-9), (t, worst)
+        assert max(bench.quantity_error_bound(q, q, eps * 1.001).values()) > t
