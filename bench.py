@@ -387,7 +387,7 @@ def small_graph_run(ctx, fj, torch, stream, reps=200):
 
 
 def serving_run(ctx, fj, n_requests=10_000, pool_size=48, seed=4, rate_fracs=(0.5, 0.8), window=64,
-                submitters=4, open_loop_s=30.0):
+                submitters=4, open_loop_s=30.0, n_log_range=(3, 6)):
     """The serving workload: a stream of solve requests that each bring their
     own graph (Erdos-Renyi or Chung-Lu with exponent U[2.1, 2.5], n
     log-uniform in [10^3, 10^6], average degree U[4, 20], weights U(0,1],
@@ -405,7 +405,7 @@ def serving_run(ctx, fj, n_requests=10_000, pool_size=48, seed=4, rate_fracs=(0.
     rng = np.random.default_rng(seed)
     pool = []
     for i in range(pool_size):
-        n = int(10 ** rng.uniform(3, 6))
+        n = int(10 ** rng.uniform(*n_log_range))
         m = max(1, int(n * rng.uniform(4, 20) / 2))
         if rng.random() < 0.5:
             gg = synth.erdos_renyi(n, m, seed=seed * 1000 + i, weighted=True)

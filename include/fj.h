@@ -89,8 +89,11 @@ enum {
  * moves with the iterate by e, its centred part or W^1/2 B e, so it is off by
  * at most eps (2 sqrt(x) + eps) where x is its value at the iterate, and
  * I_dc = D + C by the sum of two such terms.  The solve stops once every
- * such bound, relative to x minus the bound, is at most tol / 2 (half kept
- * as margin for rounding); a quantity equal to zero bounds nothing.
+ * such bound, relative to x minus the bound, is at most 0.9 tol (the rest
+ * kept as margin for rounding); a quantity equal to zero bounds nothing.
+ * In the mixed mode the first inner solve aims at 3% of opts.inner_tol
+ * (3e-7 by default, about the accuracy a float32 iteration attains; tol / 10
+ * if larger), the next at half the residual that would meet the bound.
  * info->rel_residual still reports the relative residual reached. */
 #define FJ_QUANTITY_TOL 8u
 
@@ -410,8 +413,8 @@ fj_status fj_tune_layout(fj_ctx* ctx, int64_t n, int64_t m, const int32_t* src,
  * keeps the current value) and a cap on the thread blocks of each request's
  * solve (0, the default: the device's co-resident solve blocks divided by
  * max_inflight, so that the in-flight requests run side by side, and a
- * quarter of them for a graph above the packing limit of fj_serve_pack, or
- * above 131072 nodes when packing is off; < 0 keeps the current value).
+ * quarter of them for a graph of more than 131072 nodes; < 0 keeps the
+ * current value).
  * Errors: FJ_ERR_ARG, FJ_ERR_CUDA. */
 fj_status fj_serve_config(fj_ctx* ctx, int32_t max_inflight,
                           int64_t mem_budget_bytes,

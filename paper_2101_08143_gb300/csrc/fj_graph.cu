@@ -11,8 +11,7 @@
 //      the SpMV layouts: chunks of the long rows, sliced ELL for the rest,
 //      and the work units;
 //   3. one streaming pass writes the 2m directed entries in solver
-//      numbering; a stable LSD radix sort of them by row (digits of 8 or 9
-//      bits, whichever takes fewer passes) puts every entry at
+//      numbering; a stable LSD radix sort of them by row puts every entry at
 //      its CSR position, rows keeping the input order of their entries, and
 //      its last pass also writes the sliced-ELL copy;
 //   4. the Jacobi preconditioner 1 / (1 + d_i).
@@ -30,8 +29,6 @@
 namespace fj {
 
 constexpr int kSortThreads = 512;
-constexpr int kSortItems = 8;  // items per thread per block chunk
-constexpr int kSortChunk = kSortThreads * kSortItems;
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanThreads * kScanItems;
@@ -152,13 +149,13 @@ struct EntryDst {
   float* sell_val;
 };
 
-// Digits of up to kBits bits: 8 in general; 9 where that saves a pass
-// (keys of 25 to 27 bits sort in 3 passes instead of 4).  The digit of a pass
-// is (key >> shift) & (2^width - 1) with width <= kBits.
-template <int kBits>
+// Digits of up to kBits bits: the digit of a pass is
+// (key >> shift) & (2^width - 1) with width <= kBits.
+template <int kBits, int kItems>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t N, int shift, int width,
                                                              int32_t* __restrict__ hist) {
   constexpr int kD = 1 << kBits;
+  constexpr int kSortChunk = kSortThreads * kItems;
   __shared__ int h[kD];
   const int D = 1 << width, mask = D - 1;
   for (int i = threadIdx.x; i < D; i += kSortThreads) h[i] = 0;
@@ -177,23 +174,23 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(EntrySrc s, int64_t
   for (int i = threadIdx.x; i < D; i += kSortThreads) hist[(int64_t)i * gridDim.x + blockIdx.x] = h[i];
 }
 
-// Stable scatter of one chunk of kSortChunk items.  Items are ranked in
+// Stable scatter of one chunk of kSortThreads * kItems items.  Items are ranked in
 // input order (by warp, then round, then lane), placed in shared memory in
 // digit order, and written out as one contiguous run per digit, so that
 // global stores are coalesced.  LAST: the sorted position is
 // the entry's CSR position; write the CSR and sliced-ELL copies instead of
 // the sort buffers (entries keyed n are dropped).
-template <int kBits>
+template <int kBits, int kItems>
 struct ScatterSmem {
-  int32_t key[kSortChunk];
-  int32_t col[kSortChunk];
-  float val[kSortChunk];
+  int32_t key[kSortThreads * kItems];
+  int32_t col[kSortThreads * kItems];
+  float val[kSortThreads * kItems];
   int wcnt[kSortThreads / 32][1 << kBits];
   int run[1 << kBits];
   int start[1 << kBits];
 };
 
-template <bool LAST, int kBits>
+template <bool LAST, int kBits, int kItems>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int64_t N, int shift, int width,
                                                                 const int32_t* __restrict__ offs,
                                                                 int32_t* __restrict__ okey,
@@ -204,13 +201,15 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(EntrySrc s, int6
   constexpr int kPer = kD / 32;  // digits per lane in the scan of the counts
   static_assert(kD <= kSortThreads, "one thread per digit");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ScatterSmem<kBits>& sm = *reinterpret_cast<ScatterSmem<kBits>*>(smem_raw);
+  ScatterSmem<kBits, kItems>& sm = *reinterpret_cast<ScatterSmem<kBits, kItems>*>(smem_raw);
+  constexpr int kSortChunk = kSortThreads * kItems;
+  constexpr int kSortItems = kItems;
   const int D = 1 << width, mask = D - 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int64_t cbase = (int64_t)blockIdx.x * kSortChunk;
   const int cnt = (int)((N - cbase) < kSortChunk ? (N - cbase) : kSortChunk);
-  // warp w holds chunk items w*256 + r*32 + lane (r < kSortItems), so the
+  // warp w holds chunk items w*32*kItems + r*32 + lane (r < kItems), so the
   // input order is (warp, round, lane): each warp ranks its own items
   // against warp-private digit counters, and one block-wide pass turns the
   // counters into per-warp offsets
@@ -749,16 +748,17 @@ static unsigned grid_for(int64_t work, int threads) {
 }
 
 // Stable LSD radix sort of N entries by key in [0, key_max], from buffer set
-// 0, in the fewest passes of digits of at most 8 bits, or of 9 bits where
-// that takes one pass fewer.  Buffers kb/cb/vb[2] must hold N + kPad
+// 0, in passes of digits of at most kBits bits (their widths differ by at
+// most one bit), chunks of kSortThreads * kItems entries per block.  Buffers kb/cb/vb[2] must hold N + kPad
 // elements (vb may be null: no val); returns the index (0/1) of the buffer
 // set holding the result.  With `last`, the last pass writes the CSR and
 // sliced ELL instead.  The result is the unique stable order, whatever the
 // digit widths.
-template <int kBits>
+template <int kBits, int kItems>
 static fj_status radix_passes(int32_t n, int64_t N, int bits, int32_t* kb[2], int32_t* cb[2], float* vb[2],
                               const EntryDst* last, cudaStream_t st, int* result) {
   const int passes = (bits + kBits - 1) / kBits;
+  constexpr int kSortChunk = kSortThreads * kItems;
   const int64_t nblocks = (N + kSortChunk - 1) / kSortChunk;
   int cur = 0;
   *result = 0;
@@ -766,7 +766,7 @@ static fj_status radix_passes(int32_t n, int64_t N, int bits, int32_t* kb[2], in
   int32_t* h = nullptr;
   FJ_CUDA(malloc_async(&h, ((int64_t)1 << kBits) * nblocks * sizeof(int32_t), st));
   fj_status rc = FJ_OK;
-  const size_t ssm = sizeof(ScatterSmem<kBits>);
+  const size_t ssm = sizeof(ScatterSmem<kBits, kItems>);
   const EntryDst none{};
   int shift = 0;
   for (int pass = 0; pass < passes && rc == FJ_OK; ++pass) {
@@ -776,7 +776,7 @@ static fj_status radix_passes(int32_t n, int64_t N, int bits, int32_t* kb[2], in
     const EntrySrc s{kb[cur], cb[cur], vb[cur], n};
     const int dstb = 1 - cur;
     count_launches(2);
-    k_radix_hist<kBits><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, shift, width, h);
+    k_radix_hist<kBits, kItems><<<(unsigned)nblocks, kSortThreads, 0, st>>>(s, N, shift, width, h);
     rc = exclusive_scan<int32_t>(h, ((int64_t)1 << width) * nblocks, st);
     if (rc != FJ_OK) break;
     const EntryDst& d = fin ? *last : none;
@@ -785,9 +785,9 @@ static fj_status radix_passes(int32_t n, int64_t N, int bits, int32_t* kb[2], in
       kern<<<(unsigned)nblocks, kSortThreads, ssm, st>>>(s, N, shift, width, h, kb[dstb], cb[dstb], vb[dstb], d);
     };
     if (fin)
-      launch(k_radix_scatter<true, kBits>);
+      launch(k_radix_scatter<true, kBits, kItems>);
     else
-      launch(k_radix_scatter<false, kBits>);
+      launch(k_radix_scatter<false, kBits, kItems>);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "radix sort");
     cur = dstb;
@@ -802,8 +802,11 @@ static fj_status radix_sort(int32_t n, int64_t N, int64_t key_max, int32_t* kb[2
                             const EntryDst* last, cudaStream_t st, int* result) {
   int bits = 1;
   while ((int64_t(1) << bits) <= key_max) ++bits;
-  if ((bits + 8) / 9 < (bits + 7) / 8) return radix_passes<9>(n, N, bits, kb, cb, vb, last, st, result);
-  return radix_passes<8>(n, N, bits, kb, cb, vb, last, st, result);
+  // 8-bit digits, 8 items per thread: measured against 9-bit digits (one
+  // pass fewer at 25-27 bits) and 12 or 16 items per thread, which were
+  // slower: a wider digit or a longer chunk shortens each digit's output
+  // run, and the scatter's stores lose more than the saved pass
+  return radix_passes<8, 8>(n, N, bits, kb, cb, vb, last, st, result);
 }
 
 }  // namespace fj

@@ -171,17 +171,16 @@ size_t estimate_bytes(const Request& r, int num_sms) {
 
 // Grid cap of one request's solve: the configured one, else the device's
 // co-resident solve blocks (two per SM) shared by the in-flight requests, so
-// that they run side by side instead of one at a time; a request larger than
-// the packing limit (a graph of more than pack_max_nodes nodes, or of more
-// than 131072 when packing is off) may use a quarter of them, since its
-// latency grows with its work.  The cap depends only on the request and the
+// that they run side by side instead of one at a time; a request of more
+// than kLargeRequestNodes nodes may use a quarter of them, since its latency
+// grows with its work.  The cap depends only on the request and the
 // configuration, never on the load, so a request's results are the same bits
 // alone or in a mix.
+constexpr int64_t kLargeRequestNodes = int64_t(1) << 17;
 int block_cap(const Server& S, const Request& r) {
   if (S.max_blocks > 0) return S.max_blocks;
   const int share = std::max(1, 2 * S.num_sms / std::max(1, S.max_inflight));
-  const int64_t limit = S.pack_max_nodes > 0 ? S.pack_max_nodes : (int64_t)1 << 17;
-  if (request_n(r) > limit) return std::max(share, 2 * S.num_sms / 4);
+  if (request_n(r) > kLargeRequestNodes) return std::max(share, 2 * S.num_sms / 4);
   return share;
 }
 

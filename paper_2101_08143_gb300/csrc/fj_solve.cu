@@ -99,6 +99,8 @@ struct SolveParams {
   int max_refine;
   int mode;
   int qtol;  // tol bounds each quantity's relative error (FJ_QUANTITY_TOL)
+  double qtol_frac;   // part of tol the certified bound may use
+  double first_goal;  // quantity mode: the first inner solve's reduction
   // two-solve mode (Algorithm 1 as printed): launch columns come in pairs
   // (2j: s_j solved as is, 2j+1: s_j centred), source column = c >> col_shift
   int paper;
@@ -594,10 +596,11 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
       // residual-norm reduction the next inner solve should reach
       double need = (rr64 > 0.0) ? 0.5 * P.tol * sqrt(bb[cc] / rr64) : 1.0;
       if (P.qtol) {
-        // certified per-quantity rule, with half of tol kept as margin; the
-        // first pass (q = 0 or z0) only sets the first inner solve's goal
+        // certified per-quantity rule, with part of tol kept as margin for
+        // rounding; the first pass (q = 0 or z0) only sets the first inner
+        // solve's goal
         if (init) {
-          need = 0.1 * P.tol;
+          need = P.first_goal;
           conv = bb[cc] == 0.0;
         } else {
           const int e2 = 2 * ex[cc];
@@ -605,7 +608,8 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
           const double Pq = ldexp(res[S_P * K + cc], e2);
           const double eps_goal =
               quantity_eps(ldexp(res[S_CI * K + cc], e2), ldexp(0.5 * res[S_D * K + cc], e2), Pq,
-                           Pq + 2.0 * m * ldexp(res[S_QS * K + cc], ex[cc]) + (double)n * m * m, 0.5 * P.tol);
+                           Pq + 2.0 * m * ldexp(res[S_QS * K + cc], ex[cc]) + (double)n * m * m,
+                           P.qtol_frac * P.tol);
           const double eps = ldexp(sqrt(rr64), ex[cc]);
           conv = bb[cc] == 0.0 || eps <= eps_goal;
           need = (eps > 0.0) ? 0.5 * fmin(eps_goal / eps, 1.0) : 1.0;
@@ -617,7 +621,7 @@ __device__ __forceinline__ void solve_body(const SolveParams<VI>& P, const int b
       const double rr = res[S_RR * K + cc];
       double goal = P.inner_tol;
       if (P.mode == kModeFP64) goal = need;
-      else if (need > goal) goal = need;
+      else if (need > goal || (P.qtol && init)) goal = need;
       if (fp32_mode) goal = P.tol;
       rr_goal[cc] = goal * goal * rr;
       active[cc] = !done[cc] && rr > rr_goal[cc];
@@ -988,6 +992,14 @@ static fj_status fill_params(SolveParams<VI>& P, const fj_graph* g, const double
   P.max_refine = o.max_refine;
   P.mode = mode;
   P.qtol = (o.flags & FJ_QUANTITY_TOL) ? 1 : 0;
+  // the bound may use 90% of tol; the rest covers rounding of the residual
+  // and of the quantity sums (~1e-14 relative)
+  P.qtol_frac = 0.9;
+  // first inner solve of the quantity rule: 3% of inner_tol (3e-7 by
+  // default, about the accuracy a float32 iteration attains on these
+  // systems), so that the first residual check needs at most one short
+  // second solve; float64 mode: a tenth of tol
+  P.first_goal = mode == kModeFP64 ? 0.1 * o.tol : std::max(0.03 * o.inner_tol, 0.1 * o.tol);
   P.paper = paper ? 1 : 0;
   P.z0 = z0;
   P.col_shift = paper ? 1 : 0;
