@@ -387,7 +387,7 @@ def small_graph_run(ctx, fj, torch, stream, reps=200):
 
 
 def serving_run(ctx, fj, n_requests=10_000, pool_size=48, seed=4, rate_fracs=(0.5, 0.8), window=64,
-                submitters=4, open_loop_s=30.0, n_log_range=(3, 6)):
+                submitters=4, open_loop_s=30.0, n_log_range=(3, 6), pack_max_nodes=0):
     """The serving workload: a stream of solve requests that each bring their
     own graph (Erdos-Renyi or Chung-Lu with exponent U[2.1, 2.5], n
     log-uniform in [10^3, 10^6], average degree U[4, 20], weights U(0,1],
@@ -497,7 +497,7 @@ def serving_run(ctx, fj, n_requests=10_000, pool_size=48, seed=4, rate_fracs=(0.
                                              "p99": float(np.percentile(lat2, 99))}}
     first = loops[f"{rate_fracs[0]:g}"] if rate_fracs else {"rate_per_s": None, "latency_ms": None}
     ns = np.array([pool[i][0].n for i, _ in order])
-    return {"requests": n_requests, "graph_pool": pool_size, "packed_below_nodes": 1 << 17,
+    return {"requests": n_requests, "graph_pool": pool_size, "packed_below_nodes": pack_max_nodes,
             "n_range": [int(ns.min()), int(ns.max())], "mean_n": float(ns.mean()),
             "saturation": {"requests_per_s": sat, "column_solves_per_s": cols / span, "window": window,
                            "span_s": span, "latency_ms": {"p50": float(np.percentile(lat, 50)),
@@ -964,12 +964,20 @@ def main():
         side["small_graph"] = small_graph_run(ctx, fj, torch, stream)
         side["batch"] = batch_run(ctx, fj, torch, stream)
         if not args.no_serving:
+            # the default server: every request in its own launch
             side["serving"] = serving_run(ctx, fj, n_requests=args.serving_requests)
-            # the same stream's saturation with every request in its own launch
-            fj.serve_pack(ctx, 0)
-            side["serving"]["unpacked_saturation"] = serving_run(
-                ctx, fj, n_requests=args.serving_requests, rate_fracs=())["saturation"]
+            # the same stream with graphs up to 131,072 nodes in packed batches,
+            # and a stream of small graphs (n in [1e3, 1e4]) both ways
             fj.serve_pack(ctx, 1 << 17)
+            side["serving"]["packed_saturation"] = serving_run(
+                ctx, fj, n_requests=args.serving_requests, rate_fracs=(), pack_max_nodes=1 << 17)["saturation"]
+            small = {}
+            for label, pk in (("packed", 1 << 17), ("own_launches", 0)):
+                fj.serve_pack(ctx, pk)
+                small[label] = serving_run(ctx, fj, n_requests=3000, rate_fracs=(), n_log_range=(3, 4),
+                                           pack_max_nodes=pk)["saturation"]
+            side["serving"]["small_graph_stream"] = small
+            fj.serve_pack(ctx, 0)
 
     line = None
     if rank == 0:

@@ -420,13 +420,18 @@ fj_status fj_serve_config(fj_ctx* ctx, int32_t max_inflight,
                           int64_t mem_budget_bytes,
                           int32_t max_blocks_per_request);
 
-/* Requests whose graph has at most max_nodes nodes (default 131072; 0:
- * none) are solved in packed batches: once their graphs are resident, the
+/* Requests whose graph has at most max_nodes nodes (default 0: none) are
+ * solved in packed batches: once their graphs are resident, the
  * waiting small requests are solved together, their parts of equal column
  * count packed into shared persistent launches as in fj_solve_batch, each
  * part on its own block range of at most the per-request block cap.  Larger
  * requests run their own persistent solve.  A request's results depend only
  * on its own size and the cap, so they are the same bits packed or not.
+ * Packing is off by default: on GB300 the requests' own launches, each on
+ * its slot's stream right after its graph build, served both a mixed stream
+ * (n in [1e3, 1e6]) and a stream of small graphs (n in [1e3, 1e4]) faster
+ * than packed batches, which hold every request until their slowest part
+ * ends.  Many small graphs already at hand are best given to fj_solve_batch.
  * Errors: FJ_ERR_ARG, FJ_ERR_CUDA. */
 fj_status fj_serve_pack(fj_ctx* ctx, int64_t max_nodes);
 

@@ -119,7 +119,10 @@ struct Server {
   int max_inflight = 16;
   int64_t budget = 0;
   int max_blocks = 0;  // per-request grid cap (0: automatic, see block_cap)
-  int64_t pack_max_nodes = 1 << 17;  // graphs up to this size are batched (0: never)
+  // graphs up to this size are batched (0, the default: never; measured on
+  // GB300, own launches on the slot streams serve both mixed and small-only
+  // streams faster, so packing is the caller's choice)
+  int64_t pack_max_nodes = 0;
   int64_t used = 0;
   int admitted = 0;  // requests holding a slot (admitted, not yet retired)
   uint64_t next_id = 1;

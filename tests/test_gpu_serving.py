@@ -98,7 +98,7 @@ def test_alone_and_in_a_mix_give_the_same_bits(ctx, pack):
         assert _overlapping_pairs(infos) >= 1
         _check(in_mix, g, s)
     finally:
-        fj.serve_pack(ctx, 1 << 17)
+        fj.serve_pack(ctx, 0)
 
 
 def test_packed_and_own_launch_give_the_same_bits(ctx):
@@ -115,7 +115,7 @@ def test_packed_and_own_launch_give_the_same_bits(ctx):
             assert rc == fj.FJ_OK
             out.append((q, info))
     finally:
-        fj.serve_pack(ctx, 1 << 17)
+        fj.serve_pack(ctx, 0)
     assert out[0][1]["batched"] == 1 and out[1][1]["batched"] == 0
     assert out[0][1]["blocks"] == out[1][1]["blocks"]
     assert out[0][0] == out[1][0]
@@ -158,7 +158,7 @@ def test_a_large_request_is_passed_over_at_most_32_times(ctx):
         assert tb >= info_slow["t_end_ms"]
     finally:
         fj.serve_config(ctx, max_inflight=16, mem_budget_bytes=8 << 30)
-        fj.serve_pack(ctx, 1 << 17)
+        fj.serve_pack(ctx, 0)
 
 
 @pytest.mark.slow
