@@ -5,7 +5,8 @@ cudaMalloc/cudaFree may stall the whole device) or a program whose device
 memory belongs to another allocator.  fj_solve_fixed serves them from a fixed
 scratch array inside the library.  This file checks, through the C ABI, that
 two calls in a row give the same answers as the allocating entry point
-fj_solve_ex, in every precision mode and without z, that the device's free
+fj_solve_ex, in every precision mode, with the per-quantity target and
+without z, that the device's free
 memory does not change across calls once the first call has run, and that
 requests larger than the fixed array, or host arrays, are refused.
 """
@@ -72,6 +73,30 @@ def test_fixed_matches_allocating_solve_twice(env, precision):
                 for name in fj.QUANTITY_NAMES:
                     ref = q_ref[j][name]
                     assert abs(q[j][name] - ref) <= 1e-6 * max(abs(ref), 1e-12), (name, q[j][name], ref)
+
+
+def test_fixed_with_the_quantity_target_twice(env):
+    """FJ_QUANTITY_TOL reaches the fixed entry point: two calls in a row give
+    the quantities of the allocating solve with the same target, each within
+    the target of the exact values, so within twice it of each other."""
+    torch, fj, lib, ctx = env
+    from paper_2101_08143_gb300 import synth
+    g = synth.erdos_renyi(4000, 24000, seed=14, weighted=True)
+    k = 2
+    s = synth.opinions_uniform(g.n, k, 19)
+    s_dev = torch.from_numpy(np.ascontiguousarray(s.T)).cuda()
+    opts = fj.default_opts(tol=1e-6, flags=fj.FJ_QUANTITY_TOL)
+    with ctx.upload_edges(g) as dg:
+        _, q_ref, _ = ctx.solve(dg, s_dev, opts=opts, want_z=False)
+        for _ in range(2):
+            z_dev = torch.full_like(s_dev, float("nan"))
+            rc, q, _ = _fixed(torch, fj, lib, dg, s_dev.data_ptr(), z_dev.data_ptr(), k, opts)
+            assert rc == fj.FJ_OK, lib.fj_last_error()
+            assert not torch.isnan(z_dev).any()
+            for j in range(k):
+                for name in fj.QUANTITY_NAMES:
+                    ref = q_ref[j][name]
+                    assert abs(q[j][name] - ref) <= 2e-6 * abs(ref), (name, q[j][name], ref)
 
 
 def test_fixed_without_z_and_free_memory_unchanged(env):
