@@ -423,7 +423,7 @@ class Context:
         qs = None
         if quant is not None:
             qs = [{name: getattr(quant[j], name) for name in QUANTITY_NAMES} for j in range(k)]
-        if z is not None and not _is_torch_cuda(s) and squeeze:
+        if z is not None and not _is_torch_cuda(s) and squeeze and z.ndim == 2:
             z = z[:, 0]
         d = info.as_dict()
         d["rc"] = rc

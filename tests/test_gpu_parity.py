@@ -636,3 +636,20 @@ def test_device_pointers(ctx):
     np.testing.assert_allclose(z.cpu().numpy().T, zo, atol=1e-8)
     for j in range(3):
         _check_quantities(q[j], qo[j], s[:, j], 1e-6)
+
+
+def test_host_z_out_one_and_two_dimensional(ctx):
+    """A caller's host z_out, 1-D for one opinion vector or n x k Fortran
+    order, receives z in place."""
+    g = synth.erdos_renyi(2000, 8000, seed=141, weighted=True)
+    s = synth.opinions_uniform(g.n, 2, 142)
+    zo, _ = _oracle(g, s)
+    with ctx.upload_edges(g) as dg:
+        z1 = np.empty(g.n)
+        z, _, _ = ctx.solve(dg, np.ascontiguousarray(s[:, 0]), z_out=z1)
+        assert z is z1
+        np.testing.assert_allclose(z1, zo[:, 0], atol=1e-8)
+        z2 = np.empty((g.n, 2), order="F")
+        z, _, _ = ctx.solve(dg, s, z_out=z2)
+        assert z is z2
+        np.testing.assert_allclose(z2, zo, atol=1e-8)
