@@ -119,3 +119,51 @@ def test_quantity_tol_rejected_where_undefined(ctx):
             with pytest.raises(fj.FJError) as e:
                 ctx.solve(dg, s, opts=o)
             assert e.value.code == fj.FJ_ERR_ARG
+
+
+def test_quantity_tol_degenerate_inputs(ctx):
+    """Edgeless graph (L = 0, z = s, D = 0 bounds nothing), constant opinions
+    (s_bar = 0), and 33 columns (launches of 32 and 1), all with the rule."""
+    from paper_2101_08143_gb300 import fj
+    o = fj.default_opts(tol=1e-6, flags=fj.FJ_QUANTITY_TOL)
+    g = synth.edgeless(1000)
+    s = synth.opinions_uniform(g.n, 1, 70)
+    with ctx.upload_edges(g) as dg:
+        z, q, info = ctx.solve(dg, s, opts=o)
+    np.testing.assert_allclose(z[:, 0] if z.ndim == 2 else z, s[:, 0], atol=1e-12)
+    _, qo = _oracle(g, s[:, 0])
+    for name in fo.QUANTITY_NAMES:
+        assert fo.relative_error(qo[name], q[0][name], floor=1e-12) <= 1e-6, name
+    g = synth.chung_lu(3000, 12000, 2.3, seed=71, weighted=True)
+    with ctx.upload_edges(g) as dg:
+        sc = np.full((g.n, 1), 0.25)
+        z, q, info = ctx.solve(dg, sc, opts=o)
+        np.testing.assert_allclose(z[:, 0] if z.ndim == 2 else z, 0.25, atol=1e-14)
+        assert q[0]["C_I"] == 0.0 and q[0]["D"] == 0.0 and q[0]["P"] == 0.0
+        S = synth.opinions_uniform(g.n, 33, 72)
+        z, q, info = ctx.solve(dg, S, opts=o)
+    for j in (0, 31, 32):
+        _, qo = _oracle(g, S[:, j])
+        for name in fo.QUANTITY_NAMES:
+            assert fo.relative_error(qo[name], q[j][name]) <= 1e-6, (j, name)
+
+
+def test_quantity_tol_warm_start(ctx):
+    """fj_solve_warm under the rule: from the solution of nearby opinions it
+    needs fewer iterations and still meets the target."""
+    from paper_2101_08143_gb300 import fj
+    g = synth.chung_lu(50_000, 250_000, 2.2, seed=73, weighted=True)
+    s = synth.opinions_uniform(g.n, 1, 74)[:, 0]
+    s2 = s.copy()
+    idx = np.random.default_rng(75).choice(g.n, g.n // 100, replace=False)
+    s2[idx] += np.random.default_rng(76).uniform(-0.01, 0.01, len(idx))
+    o = fj.default_opts(tol=1e-6, flags=fj.FJ_QUANTITY_TOL)
+    _, qo = _oracle(g, s2)
+    with ctx.upload_edges(g) as dg:
+        z1, _, _ = ctx.solve(dg, s, opts=o)
+        _, q_cold, i_cold = ctx.solve(dg, s2, opts=o)
+        _, q_warm, i_warm = ctx.solve(dg, s2, opts=o, z0=z1)
+    assert i_warm["iterations"] < i_cold["iterations"]
+    for q in (q_cold, q_warm):
+        for name in fo.QUANTITY_NAMES:
+            assert fo.relative_error(qo[name], q[0][name]) <= 1e-6, name
