@@ -387,7 +387,7 @@ def small_graph_run(ctx, fj, torch, stream, reps=200):
 
 
 def serving_run(ctx, fj, n_requests=10_000, pool_size=48, seed=4, rate_fracs=(0.5, 0.8), window=64,
-                submitters=4, open_loop_s=30.0, n_log_range=(3, 6), pack_max_nodes=0):
+                submitters=4, open_loop_s=30.0, n_log_range=(3, 6), pack_max_nodes=0, sequential=0):
     """The serving workload: a stream of solve requests that each bring their
     own graph (Erdos-Renyi or Chung-Lu with exponent U[2.1, 2.5], n
     log-uniform in [10^3, 10^6], average degree U[4, 20], weights U(0,1],
@@ -400,7 +400,11 @@ def serving_run(ctx, fj, n_requests=10_000, pool_size=48, seed=4, rate_fracs=(0.
     of arrivals, whichever is shorter; latency = submit to completion.  The
     generated graphs are simple, so requests pass FJ_MERGE_DUPLICATES.  Inputs
     are prepared before the clock starts; submitting copies them (the API
-    copies inputs at the call)."""
+    copies inputs at the call).  With `sequential` > 0, the first `sequential`
+    requests of the stream are also run one at a time through the blocking
+    calls (upload, solve, free), once as plain float64 solves of one opinion
+    vector per call and once as mixed-precision solves of all the request's
+    vectors per call, at the served requests' accuracy (default options)."""
     import threading
     rng = np.random.default_rng(seed)
     pool = []
@@ -496,6 +500,27 @@ def serving_run(ctx, fj, n_requests=10_000, pool_size=48, seed=4, rate_fracs=(0.
                               "latency_ms": {"p50": float(np.percentile(lat2, 50)),
                                              "p99": float(np.percentile(lat2, 99))}}
     first = loops[f"{rate_fracs[0]:g}"] if rate_fracs else {"rate_per_s": None, "latency_ms": None}
+    seq = {}
+    if sequential > 0:
+        for label, prec, per_column in (("fp64_single_rhs", fj.PREC_FP64, True),
+                                        ("mixed_multi_rhs", fj.PREC_MIXED, False)):
+            o = fj.default_opts(precision=prec)
+            cols_done = 0
+            t0 = time.perf_counter()
+            for i in range(sequential):
+                gg, sv = pool[order[i][0]]
+                k = order[i][1]
+                gr = ctx.upload(gg.n, gg.src, gg.dst, gg.w, merge_duplicates=MERGE)
+                if per_column:
+                    for j in range(k):
+                        ctx.solve(gr, np.ascontiguousarray(sv[:, j]), want_z=False, opts=o)
+                else:
+                    ctx.solve(gr, sv[:, :k], want_z=False, opts=o)
+                gr.free()
+                cols_done += k
+            dt = time.perf_counter() - t0
+            seq[label] = {"requests": sequential, "column_solves_per_s": cols_done / dt,
+                          "requests_per_s": sequential / dt}
     ns = np.array([pool[i][0].n for i, _ in order])
     return {"requests": n_requests, "graph_pool": pool_size, "packed_below_nodes": pack_max_nodes,
             "n_range": [int(ns.min()), int(ns.max())], "mean_n": float(ns.mean()),
@@ -503,7 +528,8 @@ def serving_run(ctx, fj, n_requests=10_000, pool_size=48, seed=4, rate_fracs=(0.
                            "span_s": span, "latency_ms": {"p50": float(np.percentile(lat, 50)),
                                                           "p99": float(np.percentile(lat, 99))}},
             "open_loop_rate_per_s": first["rate_per_s"], "latency_ms": first["latency_ms"],
-            "open_loops_by_fraction_of_saturation": loops}
+            "open_loops_by_fraction_of_saturation": loops,
+            **({"one_request_at_a_time": seq} if seq else {})}
 
 
 def batch_run(ctx, fj, torch, stream, count=64, seed=8, reps=3):
@@ -965,7 +991,7 @@ def main():
         side["batch"] = batch_run(ctx, fj, torch, stream)
         if not args.no_serving:
             # the default server: every request in its own launch
-            side["serving"] = serving_run(ctx, fj, n_requests=args.serving_requests)
+            side["serving"] = serving_run(ctx, fj, n_requests=args.serving_requests, sequential=300)
             # the same stream with graphs up to 131,072 nodes in packed batches,
             # and a stream of small graphs (n in [1e3, 1e4]) both ways
             fj.serve_pack(ctx, 1 << 17)
